@@ -1,0 +1,173 @@
+"""Seeded synthetic inputs for sparse w-projection imaging.
+
+This module only draws random inputs (sky images, (u, v, w) baselines, noise).
+It holds none of the imaging method's arithmetic, so both the FP64 oracle tests
+and the CUDA path can take their inputs from it.
+
+Set-up follows Section 4.1 of Wolz et al. 2013 (arXiv:1307.3424):
+  * field of view: opening angle 2 deg, planar FoV L = 2 sin(theta/2);
+  * band limit of an N-pixel image: B = N / (2L);
+  * w in the paper's normalised unit w_d = w L^2 / N, so w = w_d N / L^2;
+  * i.i.d. Gaussian noise with sigma_n = 10^(-SNR_in/20) * std(x), SNR_in = 30 dB.
+The paper's test images (M31, 30Dor) are not available; a sum of Gaussian
+blobs stands in for them (amplitudes U[0,1], widths U[1,4] px).
+
+Random numbers are drawn from numpy.random.Generator(PCG64(seed)) in the fixed
+order sky -> uv -> w -> noise.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+THETA_DEG = 2.0
+
+
+def fov_L(theta_deg: float = THETA_DEG) -> float:
+    """Planar field of view L = 2 sin(theta/2) (Section 4.1)."""
+    return 2.0 * math.sin(math.radians(theta_deg) / 2.0)
+
+
+def band_limit(N: int, L: float) -> float:
+    """B = N / (2L) (Section 4.1)."""
+    return N / (2.0 * L)
+
+
+def w_from_wd(wd, N: int, L: float):
+    """Invert w_d = w L^2 / N (Section 4.1)."""
+    return np.asarray(wd, dtype=np.float64) * N / (L * L)
+
+
+@dataclass
+class Workload:
+    name: str
+    N: int
+    n_blobs: int
+    M: int
+    uv: str = "uniform"          # "uniform" disk or "gaussian" (sigma_uv * B, truncated to the disk)
+    sigma_uv: float = 0.25
+    wd_max: float = 1.0
+    e: float = 0.99
+    W: int = 4
+    dr_iters: int = 50
+    inner_iters: int = 10
+    snr_in_db: float = 30.0
+    powerlaw: bool = False
+    extra: dict = field(default_factory=dict)
+
+
+# Small case the oracle finishes in seconds: 64x64, 20 blobs, M = 0.3 N^2.
+SMALL = Workload("blobs64_m1229", N=64, n_blobs=20, M=1229, uv="uniform",
+                 wd_max=1.0, e=0.99, dr_iters=50)
+# The paper-scale case: 256x256, 200 blobs, M = 0.5 N^2, radially Gaussian uv.
+PAPER_SCALE = Workload("blobs256_m32768", N=256, n_blobs=200, M=32768,
+                       uv="gaussian", sigma_uv=0.25, wd_max=1.0, e=0.99,
+                       dr_iters=300)
+
+
+def blob_sky(rng: np.random.Generator, N: int, n_blobs: int) -> np.ndarray:
+    """Sum of isotropic Gaussian blobs; centres U[0,N)^2, amplitude U[0,1],
+    width (Gaussian sigma in pixels) U[1,4]."""
+    cx = rng.uniform(0.0, N, n_blobs)
+    cy = rng.uniform(0.0, N, n_blobs)
+    amp = rng.uniform(0.0, 1.0, n_blobs)
+    sig = rng.uniform(1.0, 4.0, n_blobs)
+    p = np.arange(N, dtype=np.float64)
+    x = np.zeros((N, N), dtype=np.float64)
+    for b in range(n_blobs):
+        gx = np.exp(-((p - cx[b]) ** 2) / (2.0 * sig[b] ** 2))
+        gy = np.exp(-((p - cy[b]) ** 2) / (2.0 * sig[b] ** 2))
+        x += amp[b] * np.outer(gx, gy)
+    return x
+
+
+def powerlaw_field(rng: np.random.Generator, N: int, exponent: float = -2.5,
+                   top: float = 0.1) -> np.ndarray:
+    """Gaussian random field with P(k) ~ k^exponent, min-max scaled to [0, top]."""
+    k = np.fft.fftfreq(N)
+    kk = np.sqrt(k[:, None] ** 2 + k[None, :] ** 2)
+    kk[0, 0] = 1.0
+    amp = kk ** (exponent / 2.0)
+    amp[0, 0] = 0.0
+    noise = rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))
+    f = np.fft.ifft2(noise * amp).real
+    f -= f.min()
+    return top * f / max(f.max(), 1e-300)
+
+
+def uv_points(rng: np.random.Generator, M: int, B: float, N: int, kind: str,
+              sigma_uv: float = 0.25) -> np.ndarray:
+    """(u, v) in wavelengths inside the disk |uv| < B (1 - 1/N)."""
+    rmax = B * (1.0 - 1.0 / N)
+    if kind == "uniform":
+        r = rmax * np.sqrt(rng.uniform(0.0, 1.0, M))
+        th = rng.uniform(0.0, 2.0 * np.pi, M)
+        return np.stack([r * np.cos(th), r * np.sin(th)], axis=1)
+    if kind == "gaussian":
+        out = np.empty((0, 2))
+        while out.shape[0] < M:
+            cand = rng.normal(0.0, sigma_uv * B, (2 * M, 2))
+            keep = np.hypot(cand[:, 0], cand[:, 1]) < rmax
+            out = np.concatenate([out, cand[keep]], axis=0)
+        return out[:M]
+    raise ValueError(kind)
+
+
+def complex_noise(rng: np.random.Generator, M: int, sigma_n: float) -> np.ndarray:
+    """Circular complex Gaussian noise, total std sigma_n (sigma_n/sqrt(2) per part)."""
+    s = sigma_n / math.sqrt(2.0)
+    return s * rng.standard_normal(M) + 1j * s * rng.standard_normal(M)
+
+
+def noise_sigma(x: np.ndarray, snr_in_db: float) -> float:
+    """sigma_n = 10^(-SNR_in/20) * std(x), population std (Section 4.1)."""
+    return 10.0 ** (-snr_in_db / 20.0) * float(np.std(x))
+
+
+@dataclass
+class Problem:
+    wl: Workload
+    L: float
+    x: np.ndarray          # N x N float64 sky
+    uvw: np.ndarray        # M x 3 float64, wavelengths
+    wd: np.ndarray         # M normalised w
+    rng: np.random.Generator   # positioned after w; the next draw is the noise
+
+
+def make_problem(wl: Workload, seed: int = 0, M: int | None = None,
+                 wd_const: float | None = None) -> Problem:
+    """Draw sky, then uv, then w (the noise is drawn later by `draw_noise`)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    L = fov_L()
+    N = wl.N
+    M = wl.M if M is None else M
+    x = blob_sky(rng, N, wl.n_blobs)
+    if wl.powerlaw:
+        x = x + powerlaw_field(rng, N)
+    B = band_limit(N, L)
+    uv = uv_points(rng, M, B, N, wl.uv, wl.sigma_uv)
+    if wd_const is None:
+        wd = rng.uniform(0.0, wl.wd_max, M)
+    else:
+        wd = np.full(M, float(wd_const))
+    w = w_from_wd(wd, N, L)
+    uvw = np.ascontiguousarray(np.concatenate([uv, w[:, None]], axis=1))
+    return Problem(wl, L, x, uvw, wd, rng)
+
+
+def draw_noise(prob: Problem, M: int | None = None) -> tuple[np.ndarray, float]:
+    """Noise for the visibilities of `prob` (drawn after sky, uv and w)."""
+    sigma_n = noise_sigma(prob.x, prob.wl.snr_in_db)
+    M = prob.uvw.shape[0] if M is None else M
+    return complex_noise(prob.rng, M, sigma_n), sigma_n
+
+
+def random_uvw(rng: np.random.Generator, M: int, N: int, L: float,
+               wd_max: float = 1.0) -> np.ndarray:
+    """Uniform-disk (u,v) and uniform w_d in [0, wd_max], as an M x 3 array."""
+    B = band_limit(N, L)
+    uv = uv_points(rng, M, B, N, "uniform")
+    w = w_from_wd(rng.uniform(0.0, wd_max, M), N, L)
+    return np.ascontiguousarray(np.concatenate([uv, w[:, None]], axis=1))
