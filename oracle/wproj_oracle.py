@@ -303,14 +303,24 @@ def kernel_row(geo: Geometry, u: float, v: float, w: float, S: int, e: float):
     return c[o], val[o]
 
 
-def build_G(geo: Geometry, uvw: np.ndarray, e: float, S: int | None = None):
+def row_box(geo: Geometry, w: float, S) -> int:
+    """Box side of one row: S = None -> G (exact), 'rule' -> S(w) with the
+    chirp half-band h = |w| L^2 cells, an int -> that fixed size."""
+    if S is None:
+        return geo.G
+    if S == "rule":
+        return box_size_rule(geo, abs(w) * geo.L * geo.L)
+    return int(S)
+
+
+def build_G(geo: Geometry, uvw: np.ndarray, e: float, S=None):
     """CSR G (M x G^2, complex128), one thresholded kernel per visibility."""
-    S = geo.G if S is None else S
     M = uvw.shape[0]
     rows, cols, vals = [], [], []
     ptr = [0]
     for k in range(M):
-        c, v = kernel_row(geo, uvw[k, 0], uvw[k, 1], uvw[k, 2], S, e)
+        Sk = row_box(geo, uvw[k, 2], S)
+        c, v = kernel_row(geo, uvw[k, 0], uvw[k, 1], uvw[k, 2], Sk, e)
         cols.append(c)
         vals.append(v)
         ptr.append(ptr[-1] + c.size)
@@ -368,8 +378,8 @@ def phi(geo: Geometry, Gm, x):
 
 
 def phi_adj(geo: Geometry, Gm, y):
-    """Phi^H y = A Z^H F^H G^H y (complex image)."""
-    Xt = (Gm.conj().T @ np.asarray(y)).reshape(geo.G, geo.G)
+    """Phi^H y = A Z^H F^H G^H y (complex image); G^H y = conj(G^T conj(y))."""
+    Xt = np.conj(Gm.T @ np.conj(np.asarray(y))).reshape(geo.G, geo.G)
     return AZ_adj(geo, F_adj(geo, Xt))
 
 
