@@ -1,0 +1,387 @@
+"""Benchmark of the sparse w-projection hot path on the paper-scale workload.
+
+Workload (synthetic stand-in for the paper's M31/30Dor experiments): 256 x 256
+sky of 200 Gaussian blobs, M = 32768 visibilities with radially Gaussian
+(u, v) (sigma = 0.25 B, truncated to the band disk), w_d ~ U[0, 1], 2x padded
+512^2 grid, KB W = 4, e = 0.99, exact chirp, complex64 G, 30 dB noise.
+
+A step is one Douglas-Rachford iteration of the BPDN solve (10 dual
+forward-backward iterations, each a Phi and a Phi^H, plus one Phi^H and the
+prox update): 10.5 Phi+Phi^H pairs.  G is built once before the timed region
+by the same library (the build is timed separately and reported as w-kernels
+built per second).  Metric: Phi+Phi^H pairs per second, whole job.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank solves its own replica (seed = rank); no collective on
+the data path, timing is the max over ranks (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1307_3424_gb300 import synth  # noqa: E402
+
+METRIC = "phi_phiH_pairs_per_s"
+UNIT = "pairs/s"
+INNER = 10
+PAIRS_PER_STEP = INNER + 0.5          # 10 Phi + 11 Phi^H
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e", type=float, default=0.99)
+    ap.add_argument("--value-dtype", default="f32", choices=["f32", "bf16", "f16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-rows", type=int, default=64)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload_config(wl, e, extra=None):
+    cfg = {"workload": f"{wl.name}_e{e}", "N": wl.N, "G": 2 * wl.N, "M": wl.M, "e": e,
+           "uv": f"{wl.uv} sigma={wl.sigma_uv}B", "wd_max": wl.wd_max, "kb_support": wl.W,
+           "box": 2 * wl.N, "chirp": "exact", "dr_inner_iters": INNER, "pairs_per_step": PAIRS_PER_STEP}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ---------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------------
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [ln.strip().split(",") for ln in self.f.read().splitlines() if ln.strip()]
+        self.f.close()
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------------
+# oracle timing on host cores (bounded sample); shared by cpu_baseline and --impl reference
+# ---------------------------------------------------------------------------------
+
+
+def oracle_sample(wl, prob, e, n_rows, seed=0):
+    """Build the oracle rows of a random sample of visibilities and time one
+    Phi + Phi^H pair on them; the sparse part scales with the row count."""
+    from oracle import wproj_oracle as O
+    import scipy.sparse
+    geo = O.Geometry(wl.N, prob.L)
+    rng = np.random.default_rng(seed)
+    rows = np.sort(rng.choice(prob.uvw.shape[0], n_rows, replace=False))
+    t0 = time.perf_counter()
+    Gs = O.build_G(geo, prob.uvw[rows], e)
+    t_build = time.perf_counter() - t0
+    return geo, Gs, rows, t_build
+
+
+def oracle_pair_time(geo, Gs, x, y_s, M_full):
+    """Seconds of one full-size Phi + Phi^H pair, from the sample: the FFTs run at
+    full size, the sparse products on the sampled rows scaled by M / rows."""
+    from oracle import wproj_oracle as O
+    t0 = time.perf_counter()
+    X = O.F(geo, O.AZ(geo, x)).ravel()
+    t1 = time.perf_counter()
+    ys = Gs @ X
+    t2 = time.perf_counter()
+    Xt = np.conj(Gs.T @ np.conj(y_s)).reshape(geo.G, geo.G)
+    t3 = time.perf_counter()
+    O.AZ_adj(geo, O.F_adj(geo, Xt))
+    t4 = time.perf_counter()
+    scale = M_full / Gs.shape[0]
+    return (t1 - t0) + (t4 - t3) + ((t2 - t1) + (t3 - t2)) * scale, ys
+
+
+def cpu_baseline(wl, prob, e, n_rows):
+    t0 = time.perf_counter()
+    geo, Gs, rows, t_build = oracle_sample(wl, prob, e, n_rows)
+    y_s = np.ones(Gs.shape[0], complex)
+    times = []
+    for _ in range(3):
+        t, _ = oracle_pair_time(geo, Gs, prob.x, y_s, wl.M)
+        times.append(t)
+    t_pair = min(times)
+    return {"value": 1.0 / t_pair, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"{n_rows} of {wl.M} rows built by the FP64 oracle ({t_build:.1f} s, "
+                       f"{n_rows / t_build:.2f} w-kernels/s); one Phi+Phi^H pair = full-size numpy FFTs + "
+                       f"scipy CSR products on the sample scaled by M/rows; best of 3; numpy.fft and "
+                       f"scipy.sparse run single-threaded"),
+            "kernels_per_s": n_rows / t_build,
+            "wall_s": time.perf_counter() - t0}
+
+
+# ---------------------------------------------------------------------------------
+# reference arm: the oracle as the comparison program
+# ---------------------------------------------------------------------------------
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    wl = synth.PAPER_SCALE
+    prob = synth.make_problem(wl, seed=0)
+    geo, Gs, rows, t_build = oracle_sample(wl, prob, args.e, args.cpu_sample_rows)
+    y_s = np.ones(Gs.shape[0], complex)
+    for _ in range(args.warmup):
+        oracle_pair_time(geo, Gs, prob.x, y_s, wl.M)
+    tot = 0.0
+    for _ in range(args.steps):
+        for _ in range(int(math.ceil(PAIRS_PER_STEP))):
+            t, _ = oracle_pair_time(geo, Gs, prob.x, y_s, wl.M)
+            tot += t
+    # a step is PAIRS_PER_STEP pairs; ceil() pairs were run, so rescale
+    t_step = tot / args.steps * PAIRS_PER_STEP / math.ceil(PAIRS_PER_STEP)
+    value = PAIRS_PER_STEP / t_step
+    sample = (f"FP64 oracle, {args.cpu_sample_rows} of {wl.M} rows; per pair: full-size FFTs + sparse "
+              f"products on the sample scaled by M/rows; single-threaded numpy/scipy")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(wl, args.e),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------
+
+
+def read_profile_traffic(kernel: str):
+    """Per-launch DRAM traffic of a kernel from a committed ncu summary in
+    profiles/ (line 'traffic_bytes_per_launch: <n>' under '## <kernel>')."""
+    path = os.path.join(ROOT, "profiles", "traffic.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(rf"##\s*{kernel}\b.*?traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt, re.S)
+    return float(m.group(1)) if m else None
+
+
+def run_ours(args):
+    import torch
+    from paper_1307_3424_gb300 import wproj
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    wl = synth.PAPER_SCALE
+    e = args.e
+
+    prob = synth.make_problem(wl, seed=rank)
+    noise, sigma_n = synth.draw_noise(prob)
+    plan = wproj.Plan(wl.N, prob.L, value_dtype=args.value_dtype)
+    uvw_d = torch.from_numpy(prob.uvw).to(dev)
+
+    # build G (once untimed to load modules, then timed)
+    plan.build_kernels(uvw_d, e)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan.build_kernels(uvw_d, e)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    st = plan.stats()
+    nnz, M, G = st["nnz"], st["m"], plan.G
+
+    # data and solver state
+    x_d = torch.from_numpy(prob.x.astype(np.float32)).to(dev)
+    y_d = plan.phi(x_d) + torch.from_numpy(noise.astype(np.complex64)).to(dev)
+    eps = sigma_n * math.sqrt(M + 2 * math.sqrt(M))
+    _, info = plan.solve_bpdn(y_d, eps, iters=1, inner_iters=INNER)      # power iteration + 1 iteration
+    n2 = info.phi_norm2
+    for _ in range(args.warmup):
+        plan.solve_bpdn(y_d, eps, iters=1, inner_iters=INNER, phi_norm2=n2, resume=True, sync=False)
+    torch.cuda.synchronize()
+
+    # ---- timed region (device-resident inputs)
+    plan.set_timing(True)
+    plan.reset_stats()
+    x_out = torch.empty((wl.N, wl.N), dtype=torch.float32, device=dev)
+    clocks = ClockSampler(dev.index if ws == 1 else local) if rank == 0 else None
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        plan.solve_bpdn(y_d, eps, iters=1, inner_iters=INNER, phi_norm2=n2, resume=True, sync=False,
+                        x_out=x_out)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    t_ms = ev0.elapsed_time(ev1)
+    kst = plan.stats()
+    plan.set_timing(False)
+
+    # ---- end to end through the public API with host buffers
+    y_host = y_d.cpu().pin_memory()
+    x_host = torch.empty((wl.N, wl.N), dtype=torch.float32).pin_memory()
+    y_dev2 = torch.empty_like(y_d)
+    plan.reset_stats()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        y_dev2.copy_(y_host, non_blocking=True)
+        plan.solve_bpdn(y_dev2, eps, iters=1, inner_iters=INNER, phi_norm2=n2, resume=True, sync=False,
+                        x_out=x_out)
+        x_host.copy_(x_out, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_e2e_ms = e0.elapsed_time(e1)
+
+    if ws > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_ms, t_e2e_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms, t_e2e_ms = float(tt[0]), float(tt[1])
+
+    # ---- roofline of the dominant kernel (degridding or gridding)
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = json.load(open(pk))
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    b_val = 8 if args.value_dtype == "f32" else 4
+    deg_ms = kst["t_degrid_ms"] / max(1, kst["n_degrid"])
+    grid_ms = kst["t_grid_ms"] / max(1, kst["n_grid"])
+    alg_deg = nnz * b_val + M * 8 + G * G * 8
+    alg_grid = nnz * b_val + M * 8 + G * G * 8
+    stored = nnz * (b_val + 4)
+    if kst["t_degrid_ms"] >= kst["t_grid_ms"]:
+        dom, ms, alg, kname = "degrid", deg_ms, alg_deg, "k_degrid"
+    else:
+        dom, ms, alg, kname = "grid", grid_ms, alg_grid, "k_grid"
+    achieved = alg / (ms * 1e-3) / 1e9
+    roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+            "frac": achieved / hbm_peak, "traffic": read_profile_traffic(kname),
+            "peak_source": f"{peak_src} (copy bandwidth)",
+            "algorithmic_bytes_per_launch": alg, "as_stored_bytes_per_launch": stored + M * 8 + G * G * 8,
+            "as_stored_GBps": (stored + M * 8 + G * G * 8) / (ms * 1e-3) / 1e9,
+            "ms_per_launch": ms,
+            "degrid_ms": deg_ms, "grid_ms": grid_ms,
+            "degrid_frac": alg_deg / (deg_ms * 1e-3) / 1e9 / hbm_peak,
+            "grid_frac": alg_grid / (grid_ms * 1e-3) / 1e9 / hbm_peak}
+
+    value = PAIRS_PER_STEP * args.steps * ws / (t_ms * 1e-3)
+    e2e_value = PAIRS_PER_STEP * args.steps * ws / (t_e2e_ms * 1e-3)
+    out = None
+    if rank == 0:
+        cpu = None
+        if ws == 1 and not args.no_cpu_baseline:
+            cpu = cpu_baseline(wl, prob, e, args.cpu_sample_rows)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(wl, e, {"nnz": nnz, "G_bytes": nnz * (b_val + 4),
+                                              "value_dtype": args.value_dtype,
+                                              "l2": "inputs larger than L2 (G exceeds L2 many times)",
+                                              "parallelism": f"replicas x{ws}"}),
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": M * 8,
+                    "d2h_bytes_per_step": wl.N * wl.N * 4},
+            "gpu_launches": None,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "build": {"ms": build_s * 1e3, "w_kernels_per_s": M / build_s, "nnz": nnz,
+                      "nnz_per_row": nnz / M, "box": 2 * wl.N},
+            "clocks": clk,
+        }
+        out = line
+    return out, kst
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    res = run_ours(args)
+    out, kst = res
+    if out is not None:
+        out["gpu_launches"] = int(kst["launches"])
+        print(json.dumps(out))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

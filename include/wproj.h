@@ -1,0 +1,221 @@
+/*
+ * wproj.h -- C-ABI of libwproj, the GB300 (sm_103a) implementation of the
+ * sparse w-projection hot path of Wolz et al. 2013 (arXiv:1307.3424).
+ *
+ * Model.  Phi = G . F . Z . A maps a real N x N sky image x to M complex
+ * visibilities (Eq. 8 of the paper with continuous (u, v) and Kaiser-Bessel
+ * gridding):
+ *   A  divides pixel (p, q) by a(l_p) a(m_q), a the Fourier transform of the
+ *      KB gridding kernel (W taps, oversampling 2);
+ *   Z  zero-pads the image, centred, onto the G x G grid, G = 2N (the 2x
+ *      band-limit doubling of Section 4.1);
+ *   F  is the unitary 2-D DFT (1/G normalisation, e^{-2 pi i} sign of Eq. 1);
+ *   G  holds one sparse row per visibility k: the w-modulation kernel C-hat of
+ *      Eq. 8 (Section 3.1: the chirp of Eq. 4 in real space, Fourier
+ *      transformed) convolved with the KB taps at the visibility's sub-grid
+ *      offset, then sparsified by the adaptive energy threshold of Section 3.2
+ *      (the smallest set of entries holding a fraction e of the row's energy).
+ * Phi^H = A Z^H F^H G^H is its exact adjoint.  solve_bpdn solves Eq. 7 (BPDN,
+ * Dirac sparsity basis, real image) by Douglas-Rachford splitting (Section 2.3).
+ *
+ * Geometry and units.  Field of view L (direction cosines); pixel size L/N;
+ * uv cell du = 1/(2L); band limit B = N/(2L) (Section 4.1).  Baselines (u, v, w)
+ * are in wavelengths; (u, v) must lie in [-B, B).  Grid arrays are G x G,
+ * row-major, in natural FFT order (frequency q at index q mod G); the image
+ * pixel p sits at offset p - N/2.  Column index of grid cell (qu, qv) is
+ * (qu mod G) * G + (qv mod G).
+ *
+ * Conventions for every call:
+ *   - Array arguments are device pointers owned by the caller unless stated.
+ *     G, its index structures and all scratch space are owned by the plan.
+ *   - Calls return a status and never throw; wproj_last_error() gives the
+ *     message of the last failure on the calling thread.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = the legacy
+ *     default stream) unless stated.  wproj_build_kernels synchronises the
+ *     stream once (to size G).  A plan must not be used from two streams at
+ *     the same time: calls on one plan share its scratch buffers.
+ *   - Invalid sizes or parameters return WPROJ_ERR_INVALID_ARG and leave the
+ *     plan unchanged; a CUDA failure returns WPROJ_ERR_CUDA; an allocation
+ *     failure returns WPROJ_ERR_OOM.
+ */
+#ifndef WPROJ_H
+#define WPROJ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  WPROJ_OK = 0,
+  WPROJ_ERR_INVALID_ARG = 1,
+  WPROJ_ERR_OOM = 2,
+  WPROJ_ERR_CUDA = 3,
+  WPROJ_ERR_TIMEOUT = 4,
+  WPROJ_ERR_NOT_BUILT = 5,
+  WPROJ_ERR_UNSUPPORTED = 6
+} wproj_status;
+
+typedef enum { WPROJ_CHIRP_EXACT = 0, WPROJ_CHIRP_LINEAR = 1 } wproj_chirp_kind;
+typedef enum { WPROJ_EXT_FULL = 0, WPROJ_EXT_CLAMP = 1 } wproj_extension;
+typedef enum { WPROJ_VAL_F32 = 0, WPROJ_VAL_BF16 = 1, WPROJ_VAL_F16 = 2 } wproj_value_dtype;
+
+typedef struct wproj_plan wproj_plan;
+
+/* Imaging geometry of a plan. */
+typedef struct {
+  int32_t n;            /* image side N: even, 8 <= N <= 2048; the grid is G = 2N */
+  int32_t kb_support;   /* W = 4, 6 or 8 KB taps per axis; 1 = delta-gridding (single
+                           tap at floor(u/du), a == 1; exact only for on-grid u) */
+  double fov;           /* L, planar field of view in direction cosines, 0 < L, 2L^2 < 1 */
+  int32_t chirp;        /* wproj_chirp_kind: exact Eq. 4, or linear Eq. 5 (sign +) */
+  int32_t extension;    /* wproj_extension: chirp outside the field of view evaluated
+                           as is (full) or with l, m clamped to [-L/2, L/2] (clamp) */
+  int32_t box;          /* kernel box side S: 0 = rule S(w) = min(G, pow2 >= 4h+W+16),
+                           h = |w| L^2 the chirp half-band in cells; else a fixed power
+                           of two with 16 <= S <= G (S = G is exact) */
+  int32_t value_dtype;  /* wproj_value_dtype of the stored G values; bf16/f16 values are
+                           scaled per row by 1 / max|G[k,:]| (row_scale holds max|G[k,:]|) */
+} wproj_grid_desc;
+
+/* View of G held by a plan (device pointers owned by the plan; valid until the
+ * next build or the plan's destruction). */
+typedef struct {
+  int64_t m;                /* rows (visibilities) */
+  int64_t nnz;              /* stored entries */
+  int64_t n_cols;           /* G * G */
+  const int64_t *row_ptr;   /* m + 1 offsets */
+  const int32_t *col;       /* nnz column indices; within a row grouped by 32x32 grid
+                               tile (tiles ascending), row-major inside a tile */
+  const void *val;          /* nnz complex values: float2, or (bf16, bf16) / (f16, f16) pairs */
+  const float *row_scale;   /* m scales (bf16/f16), NULL for f32 */
+  int32_t value_dtype;
+} wproj_csr;
+
+/* Douglas-Rachford parameters (the paper states none; these are the defaults
+ * used by the oracle and the benchmarks). */
+typedef struct {
+  int32_t iters;        /* outer DR iterations T */
+  int32_t inner_iters;  /* dual forward-backward iterations per projection (10) */
+  double gamma_frac;    /* gamma = gamma_frac * max|Re Phi^H y| (1e-2) */
+  double lambda;        /* relaxation lambda (1.0) */
+  double phi_norm2;     /* ||Phi||^2; <= 0: estimate by power iteration */
+  int32_t power_iters;  /* power iterations when phi_norm2 <= 0 (100) */
+  int32_t resume;       /* 1: continue from the plan's current DR state (z, u, gamma,
+                           ||Phi||^2) left by the previous solve or wproj_dr_state_set;
+                           0: start from z = Re Phi^H y, u = 0 */
+} wproj_dr_params;
+
+typedef struct {
+  int32_t iters_done;
+  double phi_norm2;     /* value used for the dual step mu = 1/||Phi||^2 */
+  double gamma;
+  double final_resid;   /* ||y - Phi x||_2 of the returned x */
+  double final_l1;      /* ||x||_1 */
+} wproj_solve_info;
+
+/* Counters of a plan, for reporting. */
+typedef struct {
+  int64_t m, nnz;
+  int32_t box_min, box_max;  /* smallest / largest kernel box used by the last build */
+  int64_t segments;          /* (row, grid tile) segments of G */
+  int64_t degrid_pieces;     /* row pieces of the degridding SpMV */
+  int64_t grid_chunks;       /* tile chunks of the gridding */
+  double build_ms;           /* wall time of the last wproj_build_kernels */
+  /* accumulated device time (ms) and launches per step when timing is on */
+  double t_fft_ms, t_degrid_ms, t_grid_ms, t_reduce_ms, t_solver_ms;
+  int64_t n_fft, n_degrid, n_grid, n_reduce, n_solver;
+  int64_t launches;          /* kernels launched by Phi, Phi^H and the solver since the last reset */
+} wproj_stats;
+
+/* ---- plan ---------------------------------------------------------------- */
+
+/* Create a plan for the geometry *g on the current CUDA device.  Allocates the
+ * grid work buffers (a few G x G complex arrays).  *out receives the plan. */
+wproj_status wproj_plan_create(wproj_plan **out, const wproj_grid_desc *g);
+
+/* Free the plan and everything it owns (synchronises the device). */
+wproj_status wproj_plan_destroy(wproj_plan *p);
+
+/* ---- Part I: sparse w-kernels (Sections 3.1-3.2) -------------------------- */
+
+/* Build G for M visibilities.  uvw: device, M x 3 float64 (u, v, w in
+ * wavelengths, row-major).  e in (0, 1]: kept fraction of each row's energy
+ * (Section 3.2); each row keeps the smallest set of entries, largest moduli
+ * first, whose energy reaches (e + 1e-5) E_k, E_k the row's total (the margin
+ * covers FP32 rounding so that the kept energy reaches e E_k in exact
+ * arithmetic; e + 1e-5 >= 1 keeps the whole box).  Rejects non-finite uvw,
+ * (u, v) outside [-B, B) and m < 1 with WPROJ_ERR_INVALID_ARG (detected on the
+ * device; the plan keeps no G then).  Replaces any previous G.  Returns after
+ * the build has finished.  out (nullable) receives a view of G. */
+wproj_status wproj_build_kernels(wproj_plan *p, const double *uvw, int64_t m, double e,
+                                 void *stream, wproj_csr *out);
+
+/* View of the current G (WPROJ_ERR_NOT_BUILT before the first build). */
+wproj_status wproj_get_csr(const wproj_plan *p, wproj_csr *out);
+
+/* ---- Part II: measurement operator (Eq. 8) -------------------------------- */
+
+/* y = Phi x.  x: device N x N float32 (row-major, pixel (p, q) at p*N + q);
+ * y: device M complex (float2). */
+wproj_status wproj_phi(wproj_plan *p, const float *x, void *y, void *stream);
+
+/* Phi^H y.  y: device M float2.  x_re (nullable): N x N float32 receives
+ * Re(Phi^H y); x_cplx (nullable): N x N float2 receives the complex adjoint. */
+wproj_status wproj_phi_adj(wproj_plan *p, const void *y, float *x_re, void *x_cplx,
+                           void *stream);
+
+/* Complex-image forward operator (for the adjoint identity): x_cplx N x N float2. */
+wproj_status wproj_phi_cplx(wproj_plan *p, const void *x_cplx, void *y, void *stream);
+
+/* ---- Part III: BPDN by Douglas-Rachford (Eq. 7) --------------------------- */
+
+/* Solve min ||x||_1 s.t. ||y - Phi x||_2 <= eps over real x.  y: device M
+ * float2; x_out: device N x N float32.  prm NULL = defaults (T = 50, 10 inner
+ * iterations, gamma_frac 1e-2, lambda 1, power iteration 100).  info (nullable)
+ * makes the call synchronous and fills the summary; with info NULL the call is
+ * asynchronous. */
+wproj_status wproj_solve_bpdn(wproj_plan *p, const void *y, double eps,
+                              const wproj_dr_params *prm, float *x_out,
+                              wproj_solve_info *info, void *stream);
+
+/* ||Phi||^2 of the real-image operator by `iters` power iterations from the
+ * constant image 1/N (synchronous). */
+wproj_status wproj_power_norm2(wproj_plan *p, int32_t iters, double *out, void *stream);
+
+/* Checkpoint / resume of the Douglas-Rachford state: z (N x N float32), the dual
+ * variable u (M float2, one per visibility of the current G), gamma and ||Phi||^2.
+ * Pointers may be host or device memory (copied with cudaMemcpyDefault, then the
+ * stream is synchronised).  get needs a previous solve (WPROJ_ERR_NOT_BUILT
+ * otherwise); set makes the next solve with resume = 1 continue from the given
+ * state, which reproduces the saved run's next iterate exactly on the same GPU. */
+wproj_status wproj_dr_state_get(wproj_plan *p, float *z, void *u, double *gamma, double *phi_norm2,
+                                void *stream);
+wproj_status wproj_dr_state_set(wproj_plan *p, const float *z, const void *u, double gamma,
+                                double phi_norm2, void *stream);
+
+/* ---- utilities ------------------------------------------------------------ */
+
+/* Unnormalised 2-D DFT of `batch` n x n complex arrays (n a power of two,
+ * 16 <= n <= 4096): out[k] = sum_j in[j] exp(sign 2 pi i k.j / n), sign -1
+ * (inverse = 0) or +1 (inverse = 1).  in and out: device float2, may alias. */
+wproj_status wproj_fft2d(const void *in, void *out, int32_t n, int32_t batch, int32_t inverse,
+                         void *stream);
+
+/* Per-kernel device timing with CUDA events (0 = off, default). */
+wproj_status wproj_set_timing(wproj_plan *p, int32_t enable);
+wproj_status wproj_get_stats(wproj_plan *p, wproj_stats *out);   /* synchronises */
+wproj_status wproj_reset_stats(wproj_plan *p);
+
+/* Default DR parameters. */
+void wproj_dr_defaults(wproj_dr_params *prm);
+
+const char *wproj_last_error(void);
+const char *wproj_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WPROJ_H */

@@ -1,0 +1,68 @@
+// Shared device helpers of libwproj (product code only).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "wproj.h"
+
+namespace wproj {
+
+constexpr int kTile = 32;          // side of the grid tiles used for gridding and CSR order
+constexpr double kSelectMargin = 1e-5;   // extra kept energy fraction (covers FP32 error)
+
+// ---- complex helpers --------------------------------------------------------
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {   // conj(a) * b
+  return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+  return make_float2(a.x + b.x, a.y + b.y);
+}
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) {
+  return make_float2(a.x - b.x, a.y - b.y);
+}
+__host__ __device__ __forceinline__ float2 cscale(float2 a, float s) {
+  return make_float2(a.x * s, a.y * s);
+}
+
+// |z|^2 with a fixed rounding sequence (no FMA contraction), so every kernel
+// that recomputes a selection key gets the same bits.
+__device__ __forceinline__ float abs2_rn(float2 z) {
+  return __fadd_rn(__fmul_rn(z.x, z.x), __fmul_rn(z.y, z.y));
+}
+
+// ---- error state ------------------------------------------------------------
+void set_error(const std::string &msg);
+wproj_status fail(wproj_status st, const std::string &msg);
+wproj_status cuda_fail(cudaError_t err, const char *what);
+
+#define WPROJ_CUDA(call)                                    \
+  do {                                                      \
+    cudaError_t err__ = (call);                             \
+    if (err__ != cudaSuccess) return ::wproj::cuda_fail(err__, #call); \
+  } while (0)
+
+#define WPROJ_CHECK_LAUNCH(what)                            \
+  do {                                                      \
+    cudaError_t err__ = cudaGetLastError();                 \
+    if (err__ != cudaSuccess) return ::wproj::cuda_fail(err__, what); \
+  } while (0)
+
+#define WPROJ_TRY(expr)                                     \
+  do {                                                      \
+    wproj_status st__ = (expr);                             \
+    if (st__ != WPROJ_OK) return st__;                      \
+  } while (0)
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+inline int ilog2(int64_t n) { int l = 0; while ((int64_t(1) << l) < n) ++l; return l; }
+inline bool is_pow2(int64_t n) { return n > 0 && (n & (n - 1)) == 0; }
+
+}  // namespace wproj

@@ -1,0 +1,409 @@
+// 2-D FFT passes of libwproj.
+//
+//  * Phi  (F Z A):   row pass over the N image rows with the zero-padding and
+//    the KB correction 1/(a(l) a(m)) fused into the load, then a column pass
+//    over all G columns that reads only the N non-zero rows.
+//  * Phi^H (A Z^H F^H): column pass over the G columns that keeps only the N
+//    image rows, then a row pass over those rows that keeps only the N image
+//    columns, fused with the correction and Re(.) (or z - Re(.) for the
+//    Douglas-Rachford dual step).
+//  * The kernel build: batched S x S inverse transforms of the chirp times the
+//    KB tap polynomial, with the chirp generated in the first pass's load.
+#include "build.cuh"
+#include "fft.cuh"
+#include "plan.h"
+
+namespace wproj {
+
+namespace {
+
+__global__ void k_twiddles(float2 *tw) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < 2 || i >= kTwiddleLen) return;
+  const int l = 31 - __clz(i);
+  const int n = 1 << l;
+  const int k = i - n;
+  double sn, cs;
+  sincospi(-2.0 * double(k) / double(n), &sn, &cs);
+  tw[i] = make_float2(float(cs), float(sn));
+}
+
+// padded index -> image index (or -1): offset p - N/2 sits at (p - N/2) mod G
+__device__ __forceinline__ int pad_to_img(int P, int N, int G) {
+  const int h = N >> 1;
+  if (P < h) return P + h;
+  if (P >= G - h) return P - G + h;
+  return -1;
+}
+__device__ __forceinline__ int img_to_pad(int p, int N, int G) {
+  const int h = N >> 1;
+  return (p >= h) ? p - h : p - h + G;
+}
+
+// ---- Phi: F Z A --------------------------------------------------------------
+
+template <int LOGN>
+__global__ void __launch_bounds__(RowCfg<LOGN>::T)
+k_phi_fwd_rows(const float *__restrict__ x, const float2 *__restrict__ xc,
+               const float *__restrict__ inv_a, int N, float2 *__restrict__ inter,
+               const float2 *__restrict__ tw) {
+  using Cfg = RowCfg<LOGN>;
+  constexpr int G = 1 << LOGN;
+  extern __shared__ float2 sm[];
+  const int p0 = blockIdx.x * Cfg::C;
+  for (int idx = threadIdx.x; idx < Cfg::C * G; idx += Cfg::T) {
+    const int c = idx / G, Q = idx % G;
+    const int p = p0 + c;
+    float2 v = make_float2(0.f, 0.f);
+    if (p < N) {
+      const int q = pad_to_img(Q, N, G);
+      if (q >= 0) {
+        const float s = inv_a[p] * inv_a[q];
+        if (xc) v = cscale(xc[int64_t(p) * N + q], s);
+        else v = make_float2(x[int64_t(p) * N + q] * s, 0.f);
+      }
+    }
+    sm[c * Cfg::LD + Q] = v;
+  }
+  __syncthreads();
+  fft_block<LOGN, Cfg::C, Cfg::T, -1>(sm, Cfg::LD, tw);
+  for (int idx = threadIdx.x; idx < Cfg::C * G; idx += Cfg::T) {
+    const int c = idx / G, Q = idx % G;
+    const int p = p0 + c;
+    if (p < N) inter[int64_t(p) * G + Q] = sm[c * Cfg::LD + Q];
+  }
+}
+
+template <int LOGN>
+__global__ void __launch_bounds__(ColCfg<LOGN>::T)
+k_phi_fwd_cols(const float2 *__restrict__ inter, int N, float2 *__restrict__ Xt, float scale,
+               const float2 *__restrict__ tw) {
+  using Cfg = ColCfg<LOGN>;
+  constexpr int G = 1 << LOGN;
+  extern __shared__ float2 sm[];
+  const int Q0 = blockIdx.x * Cfg::C;
+  for (int idx = threadIdx.x; idx < Cfg::C * G; idx += Cfg::T) {
+    const int P = idx / Cfg::C, c = idx % Cfg::C;
+    const int p = pad_to_img(P, N, G);
+    float2 v = make_float2(0.f, 0.f);
+    if (p >= 0 && Q0 + c < G) v = inter[int64_t(p) * G + Q0 + c];
+    sm[c * Cfg::LD + P] = v;
+  }
+  __syncthreads();
+  fft_block<LOGN, Cfg::C, Cfg::T, -1>(sm, Cfg::LD, tw);
+  for (int idx = threadIdx.x; idx < Cfg::C * G; idx += Cfg::T) {
+    const int P = idx / Cfg::C, c = idx % Cfg::C;
+    if (Q0 + c < G) Xt[int64_t(P) * G + Q0 + c] = cscale(sm[c * Cfg::LD + P], scale);
+  }
+}
+
+// ---- Phi^H: A Z^H F^H -----------------------------------------------------------
+
+template <int LOGN>
+__global__ void __launch_bounds__(ColCfg<LOGN>::T)
+k_phi_adj_cols(const float2 *__restrict__ Xt2, int N, float2 *__restrict__ inter,
+               const float2 *__restrict__ tw) {
+  using Cfg = ColCfg<LOGN>;
+  constexpr int G = 1 << LOGN;
+  extern __shared__ float2 sm[];
+  const int Q0 = blockIdx.x * Cfg::C;
+  for (int idx = threadIdx.x; idx < Cfg::C * G; idx += Cfg::T) {
+    const int P = idx / Cfg::C, c = idx % Cfg::C;
+    sm[c * Cfg::LD + P] = (Q0 + c < G) ? Xt2[int64_t(P) * G + Q0 + c] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  fft_block<LOGN, Cfg::C, Cfg::T, +1>(sm, Cfg::LD, tw);
+  for (int idx = threadIdx.x; idx < Cfg::C * N; idx += Cfg::T) {
+    const int p = idx / Cfg::C, c = idx % Cfg::C;
+    if (Q0 + c < G) inter[int64_t(p) * G + Q0 + c] = sm[c * Cfg::LD + img_to_pad(p, N, G)];
+  }
+}
+
+// mode 0: x_re = Re(v) s (and x_c = v s when given); mode 1: x_re = z - Re(v) s
+template <int LOGN>
+__global__ void __launch_bounds__(RowCfg<LOGN>::T)
+k_phi_adj_rows(const float2 *__restrict__ inter, const float *__restrict__ inv_a, int N,
+               float scale, float *__restrict__ x_re, float2 *__restrict__ x_c,
+               const float *__restrict__ z, int mode, const float2 *__restrict__ tw) {
+  using Cfg = RowCfg<LOGN>;
+  constexpr int G = 1 << LOGN;
+  extern __shared__ float2 sm[];
+  const int p0 = blockIdx.x * Cfg::C;
+  for (int idx = threadIdx.x; idx < Cfg::C * G; idx += Cfg::T) {
+    const int c = idx / G, Q = idx % G;
+    const int p = p0 + c;
+    sm[c * Cfg::LD + Q] = (p < N) ? inter[int64_t(p) * G + Q] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  fft_block<LOGN, Cfg::C, Cfg::T, +1>(sm, Cfg::LD, tw);
+  for (int idx = threadIdx.x; idx < Cfg::C * N; idx += Cfg::T) {
+    const int c = idx / N, q = idx % N;
+    const int p = p0 + c;
+    if (p >= N) continue;
+    const float s = inv_a[p] * inv_a[q] * scale;
+    const float2 v = sm[c * Cfg::LD + img_to_pad(q, N, G)];
+    const int64_t o = int64_t(p) * N + q;
+    if (mode == 0) {
+      if (x_re) x_re[o] = v.x * s;
+      if (x_c) x_c[o] = cscale(v, s);
+    } else {
+      x_re[o] = z[o] - v.x * s;
+    }
+  }
+}
+
+// ---- generic batched 2-D FFT (rows then columns) --------------------------------
+
+template <int LOGN, int DIR>
+__global__ void __launch_bounds__(RowCfg<LOGN>::T)
+k_fft_rows(const float2 *__restrict__ in, float2 *__restrict__ out, int64_t n_rows,
+           const float2 *__restrict__ tw) {
+  using Cfg = RowCfg<LOGN>;
+  constexpr int N = 1 << LOGN;
+  extern __shared__ float2 sm[];
+  const int64_t r0 = int64_t(blockIdx.x) * Cfg::C;
+  for (int idx = threadIdx.x; idx < Cfg::C * N; idx += Cfg::T) {
+    const int c = idx / N, i = idx % N;
+    sm[c * Cfg::LD + i] = (r0 + c < n_rows) ? in[(r0 + c) * N + i] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  fft_block<LOGN, Cfg::C, Cfg::T, DIR>(sm, Cfg::LD, tw);
+  for (int idx = threadIdx.x; idx < Cfg::C * N; idx += Cfg::T) {
+    const int c = idx / N, i = idx % N;
+    if (r0 + c < n_rows) out[(r0 + c) * N + i] = sm[c * Cfg::LD + i];
+  }
+}
+
+// columns of `batch` N x N arrays, flattened as batch * N global columns
+template <int LOGN, int DIR>
+__global__ void __launch_bounds__(ColCfg<LOGN>::T)
+k_fft_cols(const float2 *__restrict__ in, float2 *__restrict__ out, int64_t n_cols, float scale,
+           const float2 *__restrict__ tw) {
+  using Cfg = ColCfg<LOGN>;
+  constexpr int N = 1 << LOGN;
+  extern __shared__ float2 sm[];
+  const int64_t g0 = int64_t(blockIdx.x) * Cfg::C;
+  for (int idx = threadIdx.x; idx < Cfg::C * N; idx += Cfg::T) {
+    const int P = idx / Cfg::C, c = idx % Cfg::C;
+    const int64_t gc = g0 + c;
+    float2 v = make_float2(0.f, 0.f);
+    if (gc < n_cols) {
+      const int64_t b = gc >> LOGN, Q = gc & (N - 1);
+      v = in[(b * N + P) * N + Q];
+    }
+    sm[c * Cfg::LD + P] = v;
+  }
+  __syncthreads();
+  fft_block<LOGN, Cfg::C, Cfg::T, DIR>(sm, Cfg::LD, tw);
+  for (int idx = threadIdx.x; idx < Cfg::C * N; idx += Cfg::T) {
+    const int P = idx / Cfg::C, c = idx % Cfg::C;
+    const int64_t gc = g0 + c;
+    if (gc < n_cols) {
+      const int64_t b = gc >> LOGN, Q = gc & (N - 1);
+      out[(b * N + P) * N + Q] = cscale(sm[c * Cfg::LD + P], scale);
+    }
+  }
+}
+
+// ---- kernel build: S x S boxes ---------------------------------------------------
+
+// f[P][Q] = Au[P] Av[Q] e^{2 pi i w g(x)}: the chirp (Eq. 4 / Eq. 5) times the KB
+// tap polynomial, at box offsets P' = P (P < S/2) or P - S; Au, Av carry the
+// separable part of the phase, w (l^2 + m^2) / 2, and the taps.
+__device__ __forceinline__ float2 box_value(const BoxBatch &bb, int b, int P, int Q) {
+  const float2 a = bb.Au[int64_t(b) * bb.S + P];
+  const float2 c = bb.Av[int64_t(b) * bb.S + Q];
+  float2 f = cmul(a, c);
+  const int mode = bb.mode[b];
+  if (mode == 1) {
+    // exact chirp: phase w (1 - n) = w x / 2 + w g(x), g = x^2 / (2 (1 + n)^2), the
+    // remainder |w g| <= 1/4 cycle so FP32 keeps it to ~1e-7 cycles
+    const float x = bb.lsq[P] + bb.lsq[Q];
+    const float n = sqrtf(1.f - x);
+    const float d = 1.f + n;
+    const float g = (x * x) / (2.f * d * d);
+    float sn, cs;
+    sincospif(2.f * (bb.wf[b] * g), &sn, &cs);
+    f = cmul(f, make_float2(cs, sn));
+  } else if (mode == 2) {
+    // large w: the full phase argument in FP64, reduced mod 1
+    const double l = bb.lcoord[P], m = bb.lcoord[Q];
+    const double x = l * l + m * m;
+    const double ph = bb.wd[b] * x / (1.0 + sqrt(1.0 - x));
+    const double fr = ph - floor(ph);
+    float sn, cs;
+    sincospif(2.f * float(fr), &sn, &cs);
+    f = cmul(f, make_float2(cs, sn));
+  }
+  return f;
+}
+
+template <int LOGN>
+__global__ void __launch_bounds__(RowCfg<LOGN>::T)
+k_box_rows(BoxBatch bb, const float2 *__restrict__ tw) {
+  using Cfg = RowCfg<LOGN>;
+  constexpr int S = 1 << LOGN;
+  extern __shared__ float2 sm[];
+  const int64_t n_rows = int64_t(bb.nb) * S;
+  const int64_t r0 = int64_t(blockIdx.x) * Cfg::C;
+  for (int idx = threadIdx.x; idx < Cfg::C * S; idx += Cfg::T) {
+    const int c = idx / S, Q = idx % S;
+    const int64_t r = r0 + c;
+    float2 v = make_float2(0.f, 0.f);
+    if (r < n_rows) v = box_value(bb, int(r >> LOGN), int(r & (S - 1)), Q);
+    sm[c * Cfg::LD + Q] = v;
+  }
+  __syncthreads();
+  fft_block<LOGN, Cfg::C, Cfg::T, +1>(sm, Cfg::LD, tw);
+  for (int idx = threadIdx.x; idx < Cfg::C * S; idx += Cfg::T) {
+    const int c = idx / S, Q = idx % S;
+    const int64_t r = r0 + c;
+    if (r < n_rows) bb.K[r * S + Q] = sm[c * Cfg::LD + Q];
+  }
+}
+
+// ---- dispatch ------------------------------------------------------------------
+
+template <class K>
+wproj_status set_smem(K kern, size_t smem) {
+  if (smem > 48 * 1024) {
+    WPROJ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  }
+  return WPROJ_OK;
+}
+
+template <int LOGN>
+wproj_status phi_fwd_impl(wproj_plan *p, const float *x, const float2 *xc, float2 *Xt, cudaStream_t s) {
+  const int N = p->g.N, G = p->g.G;
+  const float2 *tw = p->twiddle.as<float2>();
+  float2 *inter = p->inter.as<float2>();
+  {
+    using Cfg = RowCfg<LOGN>;
+    WPROJ_TRY(set_smem(k_phi_fwd_rows<LOGN>, Cfg::SMEM));
+    k_phi_fwd_rows<LOGN><<<ceil_div(N, Cfg::C), Cfg::T, Cfg::SMEM, s>>>(x, xc, p->inv_a.as<float>(), N, inter, tw);
+    WPROJ_CHECK_LAUNCH("phi fwd rows");
+  }
+  {
+    using Cfg = ColCfg<LOGN>;
+    WPROJ_TRY(set_smem(k_phi_fwd_cols<LOGN>, Cfg::SMEM));
+    k_phi_fwd_cols<LOGN><<<ceil_div(G, Cfg::C), Cfg::T, Cfg::SMEM, s>>>(inter, N, Xt, 1.0f / G, tw);
+    WPROJ_CHECK_LAUNCH("phi fwd cols");
+  }
+  return WPROJ_OK;
+}
+
+template <int LOGN>
+wproj_status phi_adj_impl(wproj_plan *p, const float2 *Xt2, float *x_re, float2 *x_c, const float *z,
+                          int mode, cudaStream_t s) {
+  const int N = p->g.N, G = p->g.G;
+  const float2 *tw = p->twiddle.as<float2>();
+  float2 *inter = p->inter.as<float2>();
+  {
+    using Cfg = ColCfg<LOGN>;
+    WPROJ_TRY(set_smem(k_phi_adj_cols<LOGN>, Cfg::SMEM));
+    k_phi_adj_cols<LOGN><<<ceil_div(G, Cfg::C), Cfg::T, Cfg::SMEM, s>>>(Xt2, N, inter, tw);
+    WPROJ_CHECK_LAUNCH("phi adj cols");
+  }
+  {
+    using Cfg = RowCfg<LOGN>;
+    WPROJ_TRY(set_smem(k_phi_adj_rows<LOGN>, Cfg::SMEM));
+    k_phi_adj_rows<LOGN><<<ceil_div(N, Cfg::C), Cfg::T, Cfg::SMEM, s>>>(
+        inter, p->inv_a.as<float>(), N, 1.0f / G, x_re, x_c, z, mode, tw);
+    WPROJ_CHECK_LAUNCH("phi adj rows");
+  }
+  return WPROJ_OK;
+}
+
+template <int LOGN>
+wproj_status fft2d_impl(const float2 *in, float2 *out, int batch, int inverse, const float2 *tw,
+                        cudaStream_t s) {
+  constexpr int N = 1 << LOGN;
+  using RC = RowCfg<LOGN>;
+  using CC = ColCfg<LOGN>;
+  const int64_t rows = int64_t(batch) * N;
+  if (inverse) {
+    WPROJ_TRY(set_smem(k_fft_rows<LOGN, +1>, RC::SMEM));
+    WPROJ_TRY(set_smem(k_fft_cols<LOGN, +1>, CC::SMEM));
+    k_fft_rows<LOGN, +1><<<ceil_div(rows, RC::C), RC::T, RC::SMEM, s>>>(in, out, rows, tw);
+    k_fft_cols<LOGN, +1><<<ceil_div(rows, CC::C), CC::T, CC::SMEM, s>>>(out, out, rows, 1.f, tw);
+  } else {
+    WPROJ_TRY(set_smem(k_fft_rows<LOGN, -1>, RC::SMEM));
+    WPROJ_TRY(set_smem(k_fft_cols<LOGN, -1>, CC::SMEM));
+    k_fft_rows<LOGN, -1><<<ceil_div(rows, RC::C), RC::T, RC::SMEM, s>>>(in, out, rows, tw);
+    k_fft_cols<LOGN, -1><<<ceil_div(rows, CC::C), CC::T, CC::SMEM, s>>>(out, out, rows, 1.f, tw);
+  }
+  WPROJ_CHECK_LAUNCH("fft2d");
+  return WPROJ_OK;
+}
+
+template <int LOGN>
+wproj_status box_fft_impl(wproj_plan *p, const BoxBatch &bb, cudaStream_t s) {
+  constexpr int S = 1 << LOGN;
+  using RC = RowCfg<LOGN>;
+  using CC = ColCfg<LOGN>;
+  const float2 *tw = p->twiddle.as<float2>();
+  const int64_t rows = int64_t(bb.nb) * S;
+  WPROJ_TRY(set_smem(k_box_rows<LOGN>, RC::SMEM));
+  WPROJ_TRY(set_smem(k_fft_cols<LOGN, +1>, CC::SMEM));
+  k_box_rows<LOGN><<<ceil_div(rows, RC::C), RC::T, RC::SMEM, s>>>(bb, tw);
+  WPROJ_CHECK_LAUNCH("box rows");
+  k_fft_cols<LOGN, +1><<<ceil_div(rows, CC::C), CC::T, CC::SMEM, s>>>(
+      bb.K, bb.K, rows, 1.0f / (float(S) * float(S)), tw);
+  WPROJ_CHECK_LAUNCH("box cols");
+  return WPROJ_OK;
+}
+
+#define WPROJ_LOGN_SWITCH(logn, CALL)                    \
+  switch (logn) {                                         \
+    case 4: return CALL(4);                               \
+    case 5: return CALL(5);                               \
+    case 6: return CALL(6);                               \
+    case 7: return CALL(7);                               \
+    case 8: return CALL(8);                               \
+    case 9: return CALL(9);                               \
+    case 10: return CALL(10);                             \
+    case 11: return CALL(11);                             \
+    case 12: return CALL(12);                             \
+    default: return fail(WPROJ_ERR_UNSUPPORTED, "FFT size out of range"); \
+  }
+
+}  // namespace
+
+wproj_status init_twiddles(wproj_plan *p, cudaStream_t s) {
+  WPROJ_TRY(p->twiddle.alloc(sizeof(float2) * kTwiddleLen));
+  k_twiddles<<<kTwiddleLen / 256, 256, 0, s>>>(p->twiddle.as<float2>());
+  WPROJ_CHECK_LAUNCH("twiddles");
+  return WPROJ_OK;
+}
+
+wproj_status phi_forward_fft(wproj_plan *p, const float *x, const float2 *xc, float2 *Xt, cudaStream_t s) {
+  ScopedTimer t(p, TC_FFT, s);
+  p->launches += 2;
+#define CALL(L) phi_fwd_impl<L>(p, x, xc, Xt, s)
+  WPROJ_LOGN_SWITCH(ilog2(p->g.G), CALL)
+#undef CALL
+}
+
+wproj_status phi_adjoint_fft(wproj_plan *p, const float2 *Xt2, float *x_re, float2 *x_cplx,
+                             const float *z, int mode, cudaStream_t s) {
+  ScopedTimer t(p, TC_FFT, s);
+  p->launches += 2;
+#define CALL(L) phi_adj_impl<L>(p, Xt2, x_re, x_cplx, z, mode, s)
+  WPROJ_LOGN_SWITCH(ilog2(p->g.G), CALL)
+#undef CALL
+}
+
+wproj_status fft2d_generic(const float2 *in, float2 *out, int n, int batch, int inverse,
+                           const float2 *tw, cudaStream_t s) {
+#define CALL(L) fft2d_impl<L>(in, out, batch, inverse, tw, s)
+  WPROJ_LOGN_SWITCH(ilog2(n), CALL)
+#undef CALL
+}
+
+wproj_status box_fft(wproj_plan *p, const BoxBatch &bb, cudaStream_t s) {
+#define CALL(L) box_fft_impl<L>(p, bb, s)
+  WPROJ_LOGN_SWITCH(ilog2(bb.S), CALL)
+#undef CALL
+}
+
+}  // namespace wproj

@@ -1,0 +1,241 @@
+// Part II: the measurement operator Phi = G F Z A (Eq. 8) and its adjoint.
+//
+//  degridding  y_k = sum_q G[k, q] X[q]          warp per row piece (<= 16384
+//              entries), partial sums reduced per row in a fixed order
+//  gridding    X'[q] = sum_k conj(G[k, q]) y_k    block per chunk of a grid
+//              tile's segment list; every warp accumulates its segments into
+//              a private shared-memory copy of the 32 x 32 tile, the copies are
+//              summed in warp order, chunk partials are summed per tile in chunk
+//              order.  No global atomics; results are bit-reproducible.
+#include "plan.h"
+
+namespace wproj {
+
+namespace {
+
+template <int VDT>
+__device__ __forceinline__ float2 load_val(const void *__restrict__ val, int64_t i) {
+  if constexpr (VDT == WPROJ_VAL_F32) {
+    return __ldg(reinterpret_cast<const float2 *>(val) + i);
+  } else if constexpr (VDT == WPROJ_VAL_BF16) {
+    const unsigned raw = __ldg(reinterpret_cast<const unsigned *>(val) + i);
+    __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162 *>(&raw);
+    return __bfloat1622float2(h);
+  } else {
+    const unsigned raw = __ldg(reinterpret_cast<const unsigned *>(val) + i);
+    __half2 h = *reinterpret_cast<const __half2 *>(&raw);
+    return __half22float2(h);
+  }
+}
+
+template <int VDT>
+__global__ void __launch_bounds__(256)
+k_degrid(int64_t n_pieces, const int32_t *__restrict__ piece_lo_row, const int64_t *__restrict__ piece_lo,
+         const int32_t *__restrict__ piece_len, const int32_t *__restrict__ col,
+         const void *__restrict__ val, const float2 *__restrict__ Xt, float2 *__restrict__ partial) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t pc = warp; pc < n_pieces; pc += nwarps) {
+    const int64_t lo = piece_lo[pc];
+    const int len = piece_len[pc];
+    float ax = 0.f, ay = 0.f, bx = 0.f, by = 0.f;
+    int i = lane;
+    for (; i + 96 < len; i += 128) {
+      const int c0 = __ldg(col + lo + i), c1 = __ldg(col + lo + i + 32);
+      const int c2 = __ldg(col + lo + i + 64), c3 = __ldg(col + lo + i + 96);
+      const float2 v0 = load_val<VDT>(val, lo + i), v1 = load_val<VDT>(val, lo + i + 32);
+      const float2 v2 = load_val<VDT>(val, lo + i + 64), v3 = load_val<VDT>(val, lo + i + 96);
+      const float2 x0 = __ldg(Xt + c0), x1 = __ldg(Xt + c1), x2 = __ldg(Xt + c2), x3 = __ldg(Xt + c3);
+      ax = fmaf(v0.x, x0.x, ax); ax = fmaf(-v0.y, x0.y, ax); ay = fmaf(v0.x, x0.y, ay); ay = fmaf(v0.y, x0.x, ay);
+      bx = fmaf(v1.x, x1.x, bx); bx = fmaf(-v1.y, x1.y, bx); by = fmaf(v1.x, x1.y, by); by = fmaf(v1.y, x1.x, by);
+      ax = fmaf(v2.x, x2.x, ax); ax = fmaf(-v2.y, x2.y, ax); ay = fmaf(v2.x, x2.y, ay); ay = fmaf(v2.y, x2.x, ay);
+      bx = fmaf(v3.x, x3.x, bx); bx = fmaf(-v3.y, x3.y, bx); by = fmaf(v3.x, x3.y, by); by = fmaf(v3.y, x3.x, by);
+    }
+    for (; i < len; i += 32) {
+      const int c0 = __ldg(col + lo + i);
+      const float2 v0 = load_val<VDT>(val, lo + i);
+      const float2 x0 = __ldg(Xt + c0);
+      ax = fmaf(v0.x, x0.x, ax); ax = fmaf(-v0.y, x0.y, ax); ay = fmaf(v0.x, x0.y, ay); ay = fmaf(v0.y, x0.x, ay);
+    }
+    ax += bx;
+    ay += by;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      ax += __shfl_xor_sync(0xffffffffu, ax, o);
+      ay += __shfl_xor_sync(0xffffffffu, ay, o);
+    }
+    if (lane == 0) partial[pc] = make_float2(ax, ay);
+  }
+  (void)piece_lo_row;
+}
+
+__global__ void k_degrid_reduce(int64_t m, const int32_t *__restrict__ row_piece_ptr,
+                                const float2 *__restrict__ partial, const float *__restrict__ row_scale,
+                                float2 *__restrict__ y) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= m) return;
+  float2 acc = make_float2(0.f, 0.f);
+  for (int j = row_piece_ptr[k]; j < row_piece_ptr[k + 1]; ++j) acc = cadd(acc, partial[j]);
+  if (row_scale) acc = cscale(acc, row_scale[k]);
+  y[k] = acc;
+}
+
+// accumulate conj(v) * yk into this warp's copy of the tile (entries of one
+// segment have distinct cells, so the lanes never collide)
+__device__ __forceinline__ void grid_acc(float2 *my, int q, float2 v, float2 yk, int logG, int Gm, int ou,
+                                         int ov, int TS) {
+  const int lu = (q >> logG) - ou, lv = (q & Gm) - ov;
+  if ((unsigned)lu >= (unsigned)TS || (unsigned)lv >= (unsigned)TS) return;   // not in this tile
+  float2 *cell = my + lu * TS + lv;
+  float2 a = *cell;
+  a.x = fmaf(v.x, yk.x, a.x); a.x = fmaf(v.y, yk.y, a.x);
+  a.y = fmaf(v.x, yk.y, a.y); a.y = fmaf(-v.y, yk.x, a.y);
+  *cell = a;
+}
+
+template <int VDT, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
+k_grid(const int32_t *__restrict__ chunk_tile, const int64_t *__restrict__ chunk_lo,
+       const int64_t *__restrict__ chunk_hi, const SegMeta *__restrict__ meta,
+       const int32_t *__restrict__ col, const void *__restrict__ val, const float *__restrict__ row_scale,
+       const float2 *__restrict__ y, int logG, int TS, int nT, float2 *__restrict__ partial) {
+  extern __shared__ float2 acc[];   // [WARPS][TS*TS]
+  const int c = blockIdx.x;
+  const int tile = chunk_tile[c];
+  const int tu = tile / nT, tv = tile % nT;
+  const int cells = TS * TS;
+  for (int i = threadIdx.x; i < WARPS * cells; i += blockDim.x) acc[i] = make_float2(0.f, 0.f);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float2 *my = acc + w * cells;
+  const int64_t lo = chunk_lo[c], hi = chunk_hi[c];
+  const int Gm = (1 << logG) - 1;
+  const int ou = tu * TS, ov = tv * TS;
+  int64_t j = lo + w;
+  SegMeta cur;
+  if (j < hi) cur = meta[j];
+  for (; j < hi; j += WARPS) {
+    // prefetch the next segment's descriptor while this one streams
+    SegMeta nxt;
+    const bool more = j + WARPS < hi;
+    if (more) nxt = meta[j + WARPS];
+    float2 yk = __ldg(y + cur.row);
+    if (row_scale) yk = cscale(yk, __ldg(row_scale + cur.row));
+    const int64_t off = cur.off;
+    const int n = cur.cnt;
+    int i = lane;
+    for (; i + 96 < n; i += 128) {
+      const int q0 = __ldg(col + off + i), q1 = __ldg(col + off + i + 32);
+      const int q2 = __ldg(col + off + i + 64), q3 = __ldg(col + off + i + 96);
+      const float2 v0 = load_val<VDT>(val, off + i), v1 = load_val<VDT>(val, off + i + 32);
+      const float2 v2 = load_val<VDT>(val, off + i + 64), v3 = load_val<VDT>(val, off + i + 96);
+      grid_acc(my, q0, v0, yk, logG, Gm, ou, ov, TS);
+      grid_acc(my, q1, v1, yk, logG, Gm, ou, ov, TS);
+      grid_acc(my, q2, v2, yk, logG, Gm, ou, ov, TS);
+      grid_acc(my, q3, v3, yk, logG, Gm, ou, ov, TS);
+    }
+    for (; i < n; i += 32) grid_acc(my, __ldg(col + off + i), load_val<VDT>(val, off + i), yk, logG, Gm, ou, ov, TS);
+    if (more) cur = nxt;
+  }
+  __syncthreads();
+  float2 *out = partial + int64_t(c) * cells;
+  for (int i = threadIdx.x; i < cells; i += blockDim.x) {
+    float2 s = acc[i];
+#pragma unroll
+    for (int ww = 1; ww < WARPS; ++ww) s = cadd(s, acc[ww * cells + i]);
+    out[i] = s;
+  }
+}
+
+__global__ void k_grid_reduce(const int32_t *__restrict__ tile_chunk_ptr, const float2 *__restrict__ partial,
+                              int G, int TS, int nT, float2 *__restrict__ Xt2) {
+  const int tile = blockIdx.x;
+  const int tu = tile / nT, tv = tile % nT;
+  const int cells = TS * TS;
+  const int c0 = tile_chunk_ptr[tile], c1 = tile_chunk_ptr[tile + 1];
+  for (int i = threadIdx.x; i < cells; i += blockDim.x) {
+    float2 s = make_float2(0.f, 0.f);
+    for (int c = c0; c < c1; ++c) s = cadd(s, partial[int64_t(c) * cells + i]);
+    const int lu = i / TS, lv = i % TS;
+    Xt2[int64_t(tu * TS + lu) * G + tv * TS + lv] = s;
+  }
+}
+
+constexpr int kGridWarps = 8;
+
+}  // namespace
+
+wproj_status degrid(wproj_plan *p, const float2 *Xt, float2 *y, cudaStream_t s) {
+  p->launches += 2;
+  const int blocks = (int)std::min<int64_t>(ceil_div(p->n_pieces * 32, 256), 152 * 16);
+  {
+    ScopedTimer t(p, TC_DEGRID, s);
+    switch (p->g.value_dtype) {
+      case WPROJ_VAL_F32:
+        k_degrid<WPROJ_VAL_F32><<<blocks, 256, 0, s>>>(p->n_pieces, p->piece_row.as<int32_t>(), p->piece_lo.as<int64_t>(),
+                                                       p->piece_len.as<int32_t>(), p->col.as<int32_t>(), p->val.ptr, Xt,
+                                                       p->piece_partial.as<float2>());
+        break;
+      case WPROJ_VAL_BF16:
+        k_degrid<WPROJ_VAL_BF16><<<blocks, 256, 0, s>>>(p->n_pieces, p->piece_row.as<int32_t>(), p->piece_lo.as<int64_t>(),
+                                                        p->piece_len.as<int32_t>(), p->col.as<int32_t>(), p->val.ptr, Xt,
+                                                        p->piece_partial.as<float2>());
+        break;
+      default:
+        k_degrid<WPROJ_VAL_F16><<<blocks, 256, 0, s>>>(p->n_pieces, p->piece_row.as<int32_t>(), p->piece_lo.as<int64_t>(),
+                                                       p->piece_len.as<int32_t>(), p->col.as<int32_t>(), p->val.ptr, Xt,
+                                                       p->piece_partial.as<float2>());
+    }
+    WPROJ_CHECK_LAUNCH("degrid");
+  }
+  ScopedTimer t(p, TC_REDUCE, s);
+  k_degrid_reduce<<<ceil_div(p->m, 256), 256, 0, s>>>(p->m, p->row_piece_ptr.as<int32_t>(), p->piece_partial.as<float2>(),
+                                                      p->g.value_dtype == WPROJ_VAL_F32 ? nullptr : p->row_scale.as<float>(), y);
+  WPROJ_CHECK_LAUNCH("degrid reduce");
+  return WPROJ_OK;
+}
+
+wproj_status grid(wproj_plan *p, const float2 *y, float2 *Xt2, cudaStream_t s) {
+  p->launches += 2;
+  const GridGeom &g = p->g;
+  const size_t smem = sizeof(float2) * kGridWarps * g.tile * g.tile;
+  const int logG = ilog2(g.G);
+  const float *rs = g.value_dtype == WPROJ_VAL_F32 ? nullptr : p->row_scale.as<float>();
+  {
+    ScopedTimer t(p, TC_GRID, s);
+#define LAUNCH_GRID(VDT)                                                                                    \
+  do {                                                                                                      \
+    WPROJ_CUDA(cudaFuncSetAttribute(k_grid<VDT, kGridWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+    k_grid<VDT, kGridWarps><<<(unsigned)p->n_chunks, kGridWarps * 32, smem, s>>>(                           \
+        p->chunk_tile.as<int32_t>(), p->chunk_lo.as<int64_t>(), p->chunk_hi.as<int64_t>(),                  \
+        p->seg_meta.as<SegMeta>(), p->col.as<int32_t>(), p->val.ptr, rs, y, logG, g.tile, g.nT,             \
+        p->grid_partial.as<float2>());                                                                      \
+  } while (0)
+    switch (g.value_dtype) {
+      case WPROJ_VAL_F32: LAUNCH_GRID(WPROJ_VAL_F32); break;
+      case WPROJ_VAL_BF16: LAUNCH_GRID(WPROJ_VAL_BF16); break;
+      default: LAUNCH_GRID(WPROJ_VAL_F16);
+    }
+#undef LAUNCH_GRID
+    WPROJ_CHECK_LAUNCH("grid");
+  }
+  ScopedTimer t(p, TC_REDUCE, s);
+  k_grid_reduce<<<g.nT * g.nT, 256, 0, s>>>(p->tile_chunk_ptr.as<int32_t>(), p->grid_partial.as<float2>(), g.G, g.tile,
+                                             g.nT, Xt2);
+  WPROJ_CHECK_LAUNCH("grid reduce");
+  return WPROJ_OK;
+}
+
+wproj_status apply_phi(wproj_plan *p, const float *x, const float2 *xc, float2 *y, cudaStream_t s) {
+  WPROJ_TRY(phi_forward_fft(p, x, xc, p->Xt.as<float2>(), s));
+  return degrid(p, p->Xt.as<float2>(), y, s);
+}
+
+wproj_status apply_phi_adj(wproj_plan *p, const float2 *y, float *x_re, float2 *x_cplx, const float *z,
+                           int mode, cudaStream_t s) {
+  WPROJ_TRY(grid(p, y, p->Xt2.as<float2>(), s));
+  return phi_adjoint_fft(p, p->Xt2.as<float2>(), x_re, x_cplx, z, mode, s);
+}
+
+}  // namespace wproj

@@ -1,0 +1,159 @@
+// Internal state of a libwproj plan (not part of the C-ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace wproj {
+
+// Owning device allocation.
+struct DevBuf {
+  void *ptr = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf &) = delete;
+  DevBuf &operator=(const DevBuf &) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+  }
+  wproj_status alloc(size_t n);           // exact size, contents undefined
+  wproj_status ensure(size_t n);          // grow (contents discarded)
+  template <class T> T *as() const { return static_cast<T *>(ptr); }
+};
+
+// One (row, tile) segment of G as the gridding reads it: entries [off, off+cnt)
+// of row `row`, all inside one grid tile.
+struct __align__(16) SegMeta {
+  long long off;
+  int cnt;
+  int row;
+};
+
+// Timing accumulator for one class of kernels.
+enum TimerClass { TC_FFT = 0, TC_DEGRID, TC_GRID, TC_REDUCE, TC_SOLVER, TC_COUNT };
+
+struct EventTimer {
+  std::vector<cudaEvent_t> pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+  size_t used = 0;
+  double ms[TC_COUNT] = {0};
+  int64_t count[TC_COUNT] = {0};
+  ~EventTimer();
+  cudaEvent_t get();
+};
+
+struct GridGeom {
+  int N, G, W;
+  double L, du, B, beta;
+  int chirp, extension, box;
+  int value_dtype;
+  int nT;        // tiles per axis = G / tile
+  int tile;      // tile side (min(32, G))
+};
+
+}  // namespace wproj
+
+struct wproj_plan {
+  wproj::GridGeom g;
+  int device = 0;
+
+  // constant tables
+  wproj::DevBuf twiddle;     // float2[kTwiddleLen]
+  wproj::DevBuf inv_a;       // float[N]: 1 / a(l_p)
+
+  // G
+  bool built = false;
+  int64_t m = 0, nnz = 0;
+  int box_min = 0, box_max = 0;
+  wproj::DevBuf row_ptr;     // int64[m+1]
+  wproj::DevBuf col;         // int32[nnz]
+  wproj::DevBuf val;         // float2 or 2x16-bit [nnz]
+  wproj::DevBuf row_scale;   // float[m]
+
+  // segments: one per (row, touched tile), ordered by row then tile
+  int64_t n_seg = 0;
+  wproj::DevBuf seg_off;     // int64[n_seg]  first entry in col/val
+  wproj::DevBuf seg_cnt;     // int32[n_seg]
+  wproj::DevBuf seg_row;     // int32[n_seg]
+  // gridding: segments sorted by tile (rows ascending), chunked by nnz
+  wproj::DevBuf tile_seg;    // int32[n_seg] segment ids
+  wproj::DevBuf seg_meta;    // SegMeta[n_seg] in tile-sorted order
+  int64_t n_chunks = 0;
+  wproj::DevBuf chunk_tile;  // int32[n_chunks]
+  wproj::DevBuf chunk_lo;    // int64[n_chunks]  positions in tile_seg
+  wproj::DevBuf chunk_hi;    // int64[n_chunks]
+  wproj::DevBuf tile_chunk_ptr;  // int32[nT*nT+1]
+  // degridding pieces
+  int64_t n_pieces = 0;
+  wproj::DevBuf piece_row;   // int32[n_pieces]
+  wproj::DevBuf piece_lo;    // int64[n_pieces]
+  wproj::DevBuf piece_len;   // int32[n_pieces]
+  wproj::DevBuf row_piece_ptr;   // int32[m+1]
+
+  // work buffers
+  wproj::DevBuf Xt;          // float2[G*G]  F Z A x
+  wproj::DevBuf Xt2;         // float2[G*G]  G^H y
+  wproj::DevBuf inter;       // float2[N*G]  between FFT passes
+  wproj::DevBuf grid_partial;    // float2[n_chunks * tile^2]
+  wproj::DevBuf piece_partial;   // float2[n_pieces]
+  wproj::DevBuf xtmp;        // float[N*N]
+  wproj::DevBuf ytmp;        // float2[m]
+  // solver buffers
+  wproj::DevBuf s_z, s_x, s_u, s_r, s_scal;   // scal: double scratch for reductions
+
+  // Douglas-Rachford state kept for resume / checkpoint
+  bool dr_valid = false;
+  double dr_phi_norm2 = 0;
+
+  double build_ms = 0;
+  int64_t launches = 0;     // kernels launched by Phi, Phi^H and the solver
+  bool timing = false;
+  wproj::EventTimer timer;
+};
+
+namespace wproj {
+
+// timing helpers (no-ops when timing is off)
+struct ScopedTimer {
+  wproj_plan *p;
+  int cls;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr, b = nullptr;
+  ScopedTimer(wproj_plan *p_, int cls_, cudaStream_t s_);
+  ~ScopedTimer();
+};
+
+// fft.cu
+wproj_status init_twiddles(wproj_plan *p, cudaStream_t s);
+wproj_status phi_forward_fft(wproj_plan *p, const float *x, const float2 *xc, float2 *Xt, cudaStream_t s);
+// mode 0: x_re = Re(...), x_cplx optional; mode 1: x_re = z - Re(...)
+wproj_status phi_adjoint_fft(wproj_plan *p, const float2 *Xt2, float *x_re, float2 *x_cplx,
+                             const float *z, int mode, cudaStream_t s);
+wproj_status fft2d_generic(const float2 *in, float2 *out, int n, int batch, int inverse,
+                           const float2 *twiddle, cudaStream_t s);
+// box FFT for the kernel build: nb boxes of S x S, in place; tables per box
+struct BoxBatch;
+wproj_status box_fft(wproj_plan *p, const BoxBatch &bb, cudaStream_t s);
+
+// ops.cu
+wproj_status degrid(wproj_plan *p, const float2 *Xt, float2 *y, cudaStream_t s);
+wproj_status grid(wproj_plan *p, const float2 *y, float2 *Xt2, cudaStream_t s);
+wproj_status apply_phi(wproj_plan *p, const float *x, const float2 *xc, float2 *y, cudaStream_t s);
+wproj_status apply_phi_adj(wproj_plan *p, const float2 *y, float *x_re, float2 *x_cplx,
+                           const float *z, int mode, cudaStream_t s);
+
+// scan.cu
+wproj_status exclusive_scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, cudaStream_t s);
+wproj_status exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s);
+// stable counting sort of ids [0, n) by key[i] in [0, n_bins): out_ids, bin_ptr[n_bins+1]
+wproj_status stable_bin_sort(const int32_t *key, int64_t n, int n_bins, int32_t *out_ids,
+                             int64_t *bin_ptr, cudaStream_t s);
+
+}  // namespace wproj

@@ -1,0 +1,321 @@
+"""Thin Python binding of libwproj (include/wproj.h).
+
+Argument marshalling only: every step runs in the CUDA library.  PyTorch
+supplies device memory (tensors passed by data pointer) and the stream
+(torch.cuda.current_stream()).  There is no CPU fallback: importing works
+without a GPU, but every call needs libwproj.so and a CUDA device and raises
+WprojError otherwise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libwproj.so")
+
+OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NOT_BUILT, ERR_UNSUPPORTED = range(7)
+CHIRP = {"exact": 0, "linear": 1}
+EXTENSION = {"full": 0, "clamp": 1}
+VALUE_DTYPE = {"f32": 0, "bf16": 1, "f16": 2}
+
+EXPORTED = [
+    "wproj_plan_create", "wproj_plan_destroy", "wproj_build_kernels", "wproj_get_csr",
+    "wproj_phi", "wproj_phi_adj", "wproj_phi_cplx", "wproj_solve_bpdn", "wproj_power_norm2",
+    "wproj_fft2d", "wproj_set_timing", "wproj_get_stats", "wproj_reset_stats",
+    "wproj_dr_defaults", "wproj_last_error", "wproj_version", "wproj_dr_state_get",
+    "wproj_dr_state_set",
+]
+
+
+class WprojError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"wproj status {status}: {msg}")
+        self.status = status
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("kb_support", ctypes.c_int32), ("fov", ctypes.c_double),
+                ("chirp", ctypes.c_int32), ("extension", ctypes.c_int32), ("box", ctypes.c_int32),
+                ("value_dtype", ctypes.c_int32)]
+
+
+class CSR(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("nnz", ctypes.c_int64), ("n_cols", ctypes.c_int64),
+                ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("val", ctypes.c_void_p),
+                ("row_scale", ctypes.c_void_p), ("value_dtype", ctypes.c_int32)]
+
+
+class DRParams(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("inner_iters", ctypes.c_int32),
+                ("gamma_frac", ctypes.c_double), ("lambda_", ctypes.c_double),
+                ("phi_norm2", ctypes.c_double), ("power_iters", ctypes.c_int32),
+                ("resume", ctypes.c_int32)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters_done", ctypes.c_int32), ("phi_norm2", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("final_resid", ctypes.c_double),
+                ("final_l1", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("nnz", ctypes.c_int64), ("box_min", ctypes.c_int32),
+                ("box_max", ctypes.c_int32), ("segments", ctypes.c_int64),
+                ("degrid_pieces", ctypes.c_int64), ("grid_chunks", ctypes.c_int64),
+                ("build_ms", ctypes.c_double), ("t_fft_ms", ctypes.c_double),
+                ("t_degrid_ms", ctypes.c_double), ("t_grid_ms", ctypes.c_double),
+                ("t_reduce_ms", ctypes.c_double), ("t_solver_ms", ctypes.c_double),
+                ("n_fft", ctypes.c_int64), ("n_degrid", ctypes.c_int64), ("n_grid", ctypes.c_int64),
+                ("n_reduce", ctypes.c_int64), ("n_solver", ctypes.c_int64),
+                ("launches", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libwproj.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise WprojError(ERR_UNSUPPORTED, f"{LIB_PATH} missing: build it with "
+                         "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    P = ctypes.POINTER
+    sig = {
+        "wproj_plan_create": [P(vp), P(GridDesc)],
+        "wproj_plan_destroy": [vp],
+        "wproj_build_kernels": [vp, vp, i64, dbl, vp, P(CSR)],
+        "wproj_get_csr": [vp, P(CSR)],
+        "wproj_phi": [vp, vp, vp, vp],
+        "wproj_phi_adj": [vp, vp, vp, vp, vp],
+        "wproj_phi_cplx": [vp, vp, vp, vp],
+        "wproj_solve_bpdn": [vp, vp, dbl, P(DRParams), vp, P(SolveInfo), vp],
+        "wproj_power_norm2": [vp, i32, P(dbl), vp],
+        "wproj_fft2d": [vp, vp, i32, i32, i32, vp],
+        "wproj_set_timing": [vp, i32],
+        "wproj_get_stats": [vp, P(Stats)],
+        "wproj_reset_stats": [vp],
+        "wproj_dr_state_get": [vp, vp, vp, P(dbl), P(dbl), vp],
+        "wproj_dr_state_set": [vp, vp, vp, dbl, dbl, vp],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    L.wproj_dr_defaults.argtypes = [P(DRParams)]
+    L.wproj_dr_defaults.restype = None
+    L.wproj_last_error.restype = ctypes.c_char_p
+    L.wproj_version.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _check(st: int):
+    if st != OK:
+        raise WprojError(st, lib().wproj_last_error().decode())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor | None):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise WprojError(ERR_INVALID_ARG, "tensor must be on a CUDA device")
+    if not t.is_contiguous():
+        raise WprojError(ERR_INVALID_ARG, "tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class _CAI:
+    """Zero-copy view of plan-owned device memory (__cuda_array_interface__)."""
+
+    def __init__(self, ptr: int, shape: tuple, typestr: str):
+        self.__cuda_array_interface__ = {"data": (ptr, False), "shape": shape,
+                                         "typestr": typestr, "version": 2, "strides": None}
+
+
+def dr_defaults() -> DRParams:
+    p = DRParams()
+    lib().wproj_dr_defaults(ctypes.byref(p))
+    return p
+
+
+@dataclass
+class CSRView:
+    m: int
+    nnz: int
+    n_cols: int
+    row_ptr: torch.Tensor
+    col: torch.Tensor
+    val: torch.Tensor          # complex64 (f32) or (nnz, 2) bf16/f16
+    row_scale: torch.Tensor | None
+    value_dtype: str
+
+
+class Plan:
+    """A libwproj plan: geometry, the built G and its work buffers."""
+
+    def __init__(self, n: int, fov: float, kb_support: int = 4, chirp: str = "exact",
+                 extension: str = "full", box="G", value_dtype: str = "f32"):
+        """box: "G" (default) the exact S = 2N box, "rule" the S(w) rule, or a
+        fixed power of two."""
+        self._h = ctypes.c_void_p()
+        self.n = n
+        self.G = 2 * n
+        self.value_dtype = value_dtype
+        box_i = 2 * n if box in ("G", None) else (0 if box == "rule" else int(box))
+        d = GridDesc(n, kb_support, float(fov), CHIRP[chirp], EXTENSION[extension], box_i,
+                     VALUE_DTYPE[value_dtype])
+        self.desc = d
+        self.m = 0
+        _check(lib().wproj_plan_create(ctypes.byref(self._h), ctypes.byref(d)))
+
+    def close(self):
+        if self._h:
+            lib().wproj_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    # ---- Part I
+    def build_kernels(self, uvw: torch.Tensor, e: float, stream=None) -> CSR:
+        if uvw.dtype != torch.float64 or uvw.dim() != 2 or uvw.shape[1] != 3:
+            raise WprojError(ERR_INVALID_ARG, "uvw must be an (M, 3) float64 tensor")
+        out = CSR()
+        _check(lib().wproj_build_kernels(self._h, _ptr(uvw), uvw.shape[0], float(e), _stream(stream),
+                                         ctypes.byref(out)))
+        self.m = int(out.m)
+        return out
+
+    def csr(self) -> CSRView:
+        """Zero-copy views of G (valid until the next build or close)."""
+        c = CSR()
+        _check(lib().wproj_get_csr(self._h, ctypes.byref(c)))
+        dev = torch.device("cuda", torch.cuda.current_device())
+        rp = torch.as_tensor(_CAI(c.row_ptr, (c.m + 1,), "<i8"), device=dev)
+        nnz = max(int(c.nnz), 0)
+        col = torch.as_tensor(_CAI(c.col, (nnz,), "<i4"), device=dev)
+        if c.value_dtype == 0:
+            val = torch.as_tensor(_CAI(c.val, (nnz, 2), "<f4"), device=dev)
+            val = torch.view_as_complex(val)
+            rs = None
+        else:
+            val = torch.as_tensor(_CAI(c.val, (nnz, 2), "<i2"), device=dev)
+            val = val.view(torch.bfloat16 if c.value_dtype == 1 else torch.float16)
+            rs = torch.as_tensor(_CAI(c.row_scale, (c.m,), "<f4"), device=dev)
+        name = {0: "f32", 1: "bf16", 2: "f16"}[c.value_dtype]
+        return CSRView(int(c.m), int(c.nnz), int(c.n_cols), rp, col, val, rs, name)
+
+    # ---- Part II
+    def phi(self, x: torch.Tensor, y: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        if x.dtype == torch.complex64:
+            return self.phi_cplx(x, y, stream)
+        if x.dtype != torch.float32 or tuple(x.shape) != (self.n, self.n):
+            raise WprojError(ERR_INVALID_ARG, f"x must be a ({self.n}, {self.n}) float32 tensor")
+        if y is None:
+            y = torch.empty(self.m, dtype=torch.complex64, device=x.device)
+        _check(lib().wproj_phi(self._h, _ptr(x), _ptr(y), _stream(stream)))
+        return y
+
+    def phi_cplx(self, x: torch.Tensor, y: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        if x.dtype != torch.complex64 or tuple(x.shape) != (self.n, self.n):
+            raise WprojError(ERR_INVALID_ARG, f"x must be a ({self.n}, {self.n}) complex64 tensor")
+        if y is None:
+            y = torch.empty(self.m, dtype=torch.complex64, device=x.device)
+        _check(lib().wproj_phi_cplx(self._h, _ptr(x), _ptr(y), _stream(stream)))
+        return y
+
+    def phi_adj(self, y: torch.Tensor, x_re: torch.Tensor | None = None, complex_out: bool = False,
+                stream=None):
+        if y.dtype != torch.complex64 or y.numel() != self.m:
+            raise WprojError(ERR_INVALID_ARG, f"y must be a complex64 tensor of {self.m} visibilities")
+        if complex_out:
+            xc = torch.empty((self.n, self.n), dtype=torch.complex64, device=y.device)
+            _check(lib().wproj_phi_adj(self._h, _ptr(y), None, _ptr(xc), _stream(stream)))
+            return xc
+        if x_re is None:
+            x_re = torch.empty((self.n, self.n), dtype=torch.float32, device=y.device)
+        _check(lib().wproj_phi_adj(self._h, _ptr(y), _ptr(x_re), None, _stream(stream)))
+        return x_re
+
+    # ---- Part III
+    def solve_bpdn(self, y: torch.Tensor, eps: float, iters: int = 50, inner_iters: int = 10,
+                   gamma_frac: float = 1e-2, lam: float = 1.0, phi_norm2: float = 0.0,
+                   power_iters: int = 100, x_out: torch.Tensor | None = None, sync: bool = True,
+                   resume: bool = False, stream=None):
+        """Douglas-Rachford BPDN.  resume=True continues from the plan's state
+        (the previous solve or dr_state_set) instead of z = Re Phi^H y, u = 0."""
+        if y.dtype != torch.complex64 or y.numel() != self.m:
+            raise WprojError(ERR_INVALID_ARG, f"y must be a complex64 tensor of {self.m} visibilities")
+        prm = DRParams(iters, inner_iters, gamma_frac, lam, phi_norm2, power_iters, 1 if resume else 0)
+        if x_out is None:
+            x_out = torch.empty((self.n, self.n), dtype=torch.float32, device=y.device)
+        info = SolveInfo() if sync else None
+        _check(lib().wproj_solve_bpdn(self._h, _ptr(y), float(eps), ctypes.byref(prm), _ptr(x_out),
+                                      ctypes.byref(info) if info is not None else None, _stream(stream)))
+        return x_out, info
+
+    def dr_state(self, stream=None):
+        """Checkpoint of the DR state: (z, u, gamma, phi_norm2), z and u on the device."""
+        dev = torch.device("cuda", torch.cuda.current_device())
+        z = torch.empty((self.n, self.n), dtype=torch.float32, device=dev)
+        u = torch.empty(self.m, dtype=torch.complex64, device=dev)
+        g, n2 = ctypes.c_double(), ctypes.c_double()
+        _check(lib().wproj_dr_state_get(self._h, _ptr(z), _ptr(u), ctypes.byref(g), ctypes.byref(n2),
+                                        _stream(stream)))
+        return z, u, g.value, n2.value
+
+    def set_dr_state(self, z: torch.Tensor, u: torch.Tensor, gamma: float, phi_norm2: float, stream=None):
+        _check(lib().wproj_dr_state_set(self._h, _ptr(z.contiguous()), _ptr(u.contiguous()), float(gamma),
+                                        float(phi_norm2), _stream(stream)))
+
+    def power_norm2(self, iters: int = 100, stream=None) -> float:
+        out = ctypes.c_double()
+        _check(lib().wproj_power_norm2(self._h, iters, ctypes.byref(out), _stream(stream)))
+        return out.value
+
+    # ---- reporting
+    def set_timing(self, on: bool):
+        _check(lib().wproj_set_timing(self._h, 1 if on else 0))
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib().wproj_get_stats(self._h, ctypes.byref(s)))
+        return s.as_dict()
+
+    def reset_stats(self):
+        _check(lib().wproj_reset_stats(self._h))
+
+
+def fft2d(x: torch.Tensor, inverse: bool = False, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Unnormalised 2-D DFT of a (batch, n, n) or (n, n) complex64 tensor."""
+    if x.dtype != torch.complex64 or x.shape[-1] != x.shape[-2]:
+        raise WprojError(ERR_INVALID_ARG, "x must be complex64 with square trailing dims")
+    n = x.shape[-1]
+    batch = x.numel() // (n * n)
+    if out is None:
+        out = torch.empty_like(x)
+    _check(lib().wproj_fft2d(_ptr(x), _ptr(out), n, batch, 1 if inverse else 0, _stream(stream)))
+    return out

@@ -1,0 +1,96 @@
+"""Parity at the paper-scale workload (N = 256, G = 512, M = 32768, radially
+Gaussian uv, w_d ~ U[0, 1], e = 0.99, complex64 G), built in the launch
+configuration the benchmark times.  The oracle cannot hold the whole G, so it
+checks sampled rows one by one (values, retained energy, cardinality) and
+sampled visibilities of Phi x; Phi^H is checked through the adjoint identity,
+which holds at any size."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import wproj_oracle as O
+from paper_1307_3424_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+N_SAMPLE = 10
+
+
+@pytest.fixture(scope="module")
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1307_3424_gb300 import wproj
+    wl = synth.PAPER_SCALE
+    prob = synth.make_problem(wl, seed=0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    plan = wproj.Plan(wl.N, prob.L)
+    plan.build_kernels(torch.from_numpy(prob.uvw).to(dev), wl.e)
+    geo = O.Geometry(wl.N, prob.L)
+    rng = np.random.default_rng(123)
+    rows = np.sort(rng.choice(wl.M, N_SAMPLE, replace=False))
+    yield dict(wl=wl, prob=prob, plan=plan, geo=geo, rows=rows, dev=dev)
+    plan.close()
+
+
+def test_sampled_rows_match_oracle(built):
+    plan, geo, prob, rows = built["plan"], built["geo"], built["prob"], built["rows"]
+    e = built["wl"].e
+    c = plan.csr()
+    rp = c.row_ptr.cpu().numpy()
+    G = geo.G
+    S = G
+    num = den = 0.0
+    for k in rows:
+        col = c.col[rp[k]:rp[k + 1]].cpu().numpy()
+        vg = c.val[rp[k]:rp[k + 1]].cpu().numpy().astype(np.complex128)
+        assert np.unique(col).size == col.size
+        K, j0u, j0v = O.kernel_box(geo, *prob.uvw[k], S)
+        su = ((col // G - j0u + G // 2) % G) - G // 2
+        sv = ((col % G - j0v + G // 2) % G) - G // 2
+        vo = K[su % S, sv % S]
+        num += np.sum(np.abs(vg - vo) ** 2)
+        den += np.sum(np.abs(vo) ** 2)
+        E = math.fsum(np.abs(K.ravel()) ** 2)
+        assert math.fsum(np.abs(vo) ** 2) >= e * E
+        n_hi = O.select_sort(K, O.box_columns(geo, j0u, j0v, S), e + 2e-5).size
+        assert col.size <= n_hi
+    assert math.sqrt(num / den) <= 1e-5
+
+
+def test_sampled_visibilities_match_oracle(built):
+    plan, geo, prob, rows, dev = built["plan"], built["geo"], built["prob"], built["rows"], built["dev"]
+    e = built["wl"].e
+    y = plan.phi(torch.from_numpy(prob.x.astype(np.float32)).to(dev)).cpu().numpy()
+    X = O.F(geo, O.AZ(geo, prob.x)).ravel()
+    ye, yh = [], []
+    for k in rows:
+        for ee, out in ((e, ye), (e + 2e-5, yh)):
+            c, v = O.kernel_row(geo, *prob.uvw[k], geo.G, ee)
+            out.append(np.sum(v * X[c]))
+    ye, yh = np.array(ye), np.array(yh)
+    d = np.linalg.norm(y[rows] - ye)
+    assert d <= 1.5 * np.linalg.norm(yh - ye) + 1e-5 * np.linalg.norm(ye), (d, np.linalg.norm(yh - ye))
+
+
+def test_adjoint_identity_full_size(built):
+    plan, dev = built["plan"], built["dev"]
+    wl = built["wl"]
+    rng = np.random.default_rng(7)
+    x = (rng.standard_normal((wl.N, wl.N)) + 1j * rng.standard_normal((wl.N, wl.N))).astype(np.complex64)
+    yv = (rng.standard_normal(wl.M) + 1j * rng.standard_normal(wl.M)).astype(np.complex64)
+    px = plan.phi_cplx(torch.from_numpy(x).to(dev)).cpu().numpy().astype(np.complex128)
+    ay = plan.phi_adj(torch.from_numpy(yv).to(dev), complex_out=True).cpu().numpy().astype(np.complex128)
+    lhs = np.vdot(yv.astype(np.complex128), px)
+    rhs = np.vdot(ay, x.astype(np.complex128))
+    assert abs(lhs - rhs) <= 1e-5 * np.linalg.norm(px) * np.linalg.norm(yv)
+
+
+def test_gridding_is_deterministic(built):
+    plan, dev, wl = built["plan"], built["dev"], built["wl"]
+    yv = torch.randn(wl.M, dtype=torch.complex64, device=dev)
+    a = plan.phi_adj(yv).clone()
+    b = plan.phi_adj(yv).clone()
+    assert torch.equal(a, b)

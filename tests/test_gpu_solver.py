@@ -1,0 +1,96 @@
+"""BPDN / Douglas-Rachford on the GPU against the FP64 oracle (Eq. 7), on the
+64 x 64, 20-blob, M = 1229 workload (e = 0.99, 50 iterations, 30 dB input SNR):
+reconstruction SNR within 0.1 dB; checkpoint/resume reproduces iterates exactly."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import wproj_oracle as O
+from paper_1307_3424_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def wp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1307_3424_gb300 import wproj
+    wproj.lib()
+    return wproj
+
+
+@pytest.fixture(scope="module")
+def small_problem():
+    wl = synth.SMALL
+    prob = synth.make_problem(wl, seed=0)
+    noise, sigma_n = synth.draw_noise(prob)
+    geo = O.Geometry(wl.N, prob.L)
+    Gm = O.build_G(geo, prob.uvw, wl.e)
+    y = O.phi(geo, Gm, prob.x) + noise
+    eps = O.epsilon_chi2(sigma_n, wl.M)
+    return dict(wl=wl, prob=prob, geo=geo, Gm=Gm, y=y, eps=eps)
+
+
+def test_dr_snr_matches_oracle(wp, small_problem):
+    sp = small_problem
+    wl, prob, geo, Gm = sp["wl"], sp["prob"], sp["geo"], sp["Gm"]
+    x_or, info_or = O.solve_bpdn(lambda v: O.phi(geo, Gm, v), lambda v: O.phi_adj(geo, Gm, v),
+                                 sp["y"], sp["eps"], wl.N, wl.dr_iters, inner_iters=wl.inner_iters)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    plan = wp.Plan(wl.N, prob.L)
+    plan.build_kernels(torch.from_numpy(prob.uvw).to(dev), wl.e)
+    yg = torch.from_numpy(sp["y"].astype(np.complex64)).to(dev)
+    x_gpu, info = plan.solve_bpdn(yg, sp["eps"], iters=wl.dr_iters, inner_iters=wl.inner_iters)
+    x_gpu = x_gpu.cpu().numpy().astype(np.float64)
+    snr_or = O.snr_db(prob.x, x_or)
+    snr_gpu = O.snr_db(prob.x, x_gpu)
+    print(f"SNR oracle {snr_or:.3f} dB, GPU {snr_gpu:.3f} dB, |Phi|^2 {info_or['phi_norm2']:.6g} vs "
+          f"{info.phi_norm2:.6g}")
+    assert abs(info.phi_norm2 - info_or["phi_norm2"]) <= 1e-4 * info_or["phi_norm2"]
+    assert abs(info.gamma - info_or["gamma"]) <= 1e-5 * info_or["gamma"]
+    assert abs(snr_gpu - snr_or) <= 0.1
+    assert np.linalg.norm(x_gpu - x_or) <= 1e-2 * np.linalg.norm(x_or)
+    # the reported residual and l1 norm are those of the returned image
+    r = np.linalg.norm(sp["y"] - O.phi(geo, Gm, x_gpu))
+    assert abs(info.final_resid - r) <= 1e-3 * r
+    assert abs(info.final_l1 - np.sum(np.abs(x_gpu))) <= 1e-5 * np.sum(np.abs(x_gpu))
+
+
+def test_checkpoint_resume_is_exact(wp, small_problem):
+    sp = small_problem
+    wl, prob = sp["wl"], sp["prob"]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    plan = wp.Plan(wl.N, prob.L)
+    plan.build_kernels(torch.from_numpy(prob.uvw).to(dev), wl.e)
+    yg = torch.from_numpy(sp["y"].astype(np.complex64)).to(dev)
+    _, info = plan.solve_bpdn(yg, sp["eps"], iters=4)
+    z, u, g, n2 = plan.dr_state()
+    xa, _ = plan.solve_bpdn(yg, sp["eps"], iters=3, resume=True)
+    xa = xa.clone()
+    plan.set_dr_state(z, u, g, n2)
+    xb, _ = plan.solve_bpdn(yg, sp["eps"], iters=3, resume=True)
+    assert torch.equal(xa, xb)
+    # a fresh plan restored from the checkpoint continues identically
+    plan2 = wp.Plan(wl.N, prob.L)
+    plan2.build_kernels(torch.from_numpy(prob.uvw).to(dev), wl.e)
+    plan2.set_dr_state(z.cpu(), u.cpu(), g, n2)
+    xc, _ = plan2.solve_bpdn(yg, sp["eps"], iters=3, resume=True)
+    assert torch.equal(xa, xc)
+    # 4 + 3 resumed iterations equal 7 straight ones
+    xd, _ = plan.solve_bpdn(yg, sp["eps"], iters=7, phi_norm2=n2)
+    assert torch.equal(xa, xd)
+
+
+def test_power_iteration_matches_oracle(wp, small_problem):
+    sp = small_problem
+    wl, prob, geo, Gm = sp["wl"], sp["prob"], sp["geo"], sp["Gm"]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    plan = wp.Plan(wl.N, prob.L)
+    plan.build_kernels(torch.from_numpy(prob.uvw).to(dev), wl.e)
+    n_gpu = plan.power_norm2(30)
+    n_or = O.power_norm2(lambda v: O.phi(geo, Gm, v), lambda v: O.phi_adj(geo, Gm, v), wl.N, 30)
+    assert abs(n_gpu - n_or) <= 1e-5 * n_or
+    assert math.isfinite(n_gpu)
