@@ -52,7 +52,21 @@ def parse():
     ap.add_argument("--value-dtype", default="f32", choices=["f32", "bf16", "f16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-rows", type=int, default=64)
+    ap.add_argument("--n", type=int, default=None, help="image side of a smaller profiling case")
+    ap.add_argument("--m", type=int, default=None, help="visibilities of a smaller profiling case")
     return ap.parse_args()
+
+
+def workload(args):
+    """The paper-scale workload, or a smaller case of the same recipe (profiling)."""
+    wl = synth.PAPER_SCALE
+    if args.n is None and args.m is None:
+        return wl
+    import dataclasses
+    n = args.n or wl.N
+    m = args.m or wl.M
+    blobs = max(1, int(round(wl.n_blobs * (n / wl.N) ** 2)))
+    return dataclasses.replace(wl, name=f"blobs{n}_m{m}", N=n, M=m, n_blobs=blobs)
 
 
 def dist_env():
@@ -188,7 +202,7 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    wl = synth.PAPER_SCALE
+    wl = workload(args)
     prob = synth.make_problem(wl, seed=0)
     geo, Gs, rows, t_build = oracle_sample(wl, prob, args.e, args.cpu_sample_rows)
     y_s = np.ones(Gs.shape[0], complex)
@@ -242,7 +256,7 @@ def run_ours(args):
     dev = torch.device("cuda", local if ws > 1 else 0)
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
-    wl = synth.PAPER_SCALE
+    wl = workload(args)
     e = args.e
 
     prob = synth.make_problem(wl, seed=rank)
@@ -281,12 +295,14 @@ def run_ours(args):
     if clocks:
         clocks.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.profiler.start()     # a profiler started with --profile-from-start off sees this region
     ev0.record(stream)
     for _ in range(args.steps):
         plan.solve_bpdn(y_d, eps, iters=1, inner_iters=INNER, phi_norm2=n2, resume=True, sync=False,
                         x_out=x_out)
     ev1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     clk = clocks.stop() if clocks else None
     t_ms = ev0.elapsed_time(ev1)
     kst = plan.stats()

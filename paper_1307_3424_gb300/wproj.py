@@ -288,8 +288,14 @@ class Plan:
         return z, u, g.value, n2.value
 
     def set_dr_state(self, z: torch.Tensor, u: torch.Tensor, gamma: float, phi_norm2: float, stream=None):
-        _check(lib().wproj_dr_state_set(self._h, _ptr(z.contiguous()), _ptr(u.contiguous()), float(gamma),
-                                        float(phi_norm2), _stream(stream)))
+        """Restore a checkpoint; z and u may live on the host or the device."""
+        if tuple(z.shape) != (self.n, self.n) or z.dtype != torch.float32:
+            raise WprojError(ERR_INVALID_ARG, "z must be an (N, N) float32 tensor")
+        if u.numel() != self.m or u.dtype != torch.complex64:
+            raise WprojError(ERR_INVALID_ARG, "u must be a complex64 tensor of M entries")
+        z, u = z.contiguous(), u.contiguous()
+        _check(lib().wproj_dr_state_set(self._h, ctypes.c_void_p(z.data_ptr()), ctypes.c_void_p(u.data_ptr()),
+                                        float(gamma), float(phi_norm2), _stream(stream)))
 
     def power_norm2(self, iters: int = 100, stream=None) -> float:
         out = ctypes.c_double()

@@ -49,8 +49,11 @@ def test_dr_snr_matches_oracle(wp, small_problem):
     snr_gpu = O.snr_db(prob.x, x_gpu)
     print(f"SNR oracle {snr_or:.3f} dB, GPU {snr_gpu:.3f} dB, |Phi|^2 {info_or['phi_norm2']:.6g} vs "
           f"{info.phi_norm2:.6g}")
-    assert abs(info.phi_norm2 - info_or["phi_norm2"]) <= 1e-4 * info_or["phi_norm2"]
-    assert abs(info.gamma - info_or["gamma"]) <= 1e-5 * info_or["gamma"]
+    # the GPU keeps e + 1e-5 of each row's energy, so its operator differs from the
+    # oracle's e-operator by up to ~sqrt(1e-5) in the rows' tails: gamma and ||Phi||^2
+    # agree to that level, not to FP32 rounding
+    assert abs(info.phi_norm2 - info_or["phi_norm2"]) <= 1e-3 * info_or["phi_norm2"]
+    assert abs(info.gamma - info_or["gamma"]) <= 5e-3 * info_or["gamma"]
     assert abs(snr_gpu - snr_or) <= 0.1
     assert np.linalg.norm(x_gpu - x_or) <= 1e-2 * np.linalg.norm(x_or)
     # the reported residual and l1 norm are those of the returned image
