@@ -166,6 +166,23 @@ wproj_status wproj_phi(wproj_plan *p, const float *x, void *y, void *stream);
 wproj_status wproj_phi_adj(wproj_plan *p, const void *y, float *x_re, void *x_cplx,
                            void *stream);
 
+/* y = Phi x, like wproj_phi, but the call allocates no device memory and uses
+ * none of the plan's work buffers.  (The paper has no counterpart: this is a
+ * deployment variant.)  It is for callers that cannot call cudaMalloc while
+ * they run: programs whose device memory is reserved up front by another
+ * runtime or pool allocator (a cudaMalloc there fails or escapes the pool's
+ * accounting), and loops that cannot afford the device-wide synchronisation
+ * cudaMalloc and cudaFree imply.  Its scratch (FFT intermediate, padded
+ * spectrum, degridding partial sums) lives in one fixed array of 16 MiB that
+ * every GPU loading this part of the library holds until the process exits;
+ * plans whose scratch would exceed it (in practice N > 512) are rejected with
+ * WPROJ_ERR_INVALID_ARG.  The first call on a device looks up that array's
+ * device address; make that first call before any stream capture.  All calls
+ * share the one array and leave their data in it: calls that overlap on the
+ * GPU (other streams, other threads, other plans) race and must be serialised
+ * by the caller.  x, y and the built G as for wproj_phi. */
+wproj_status wproj_phi_noalloc(wproj_plan *p, const float *x, void *y, void *stream);
+
 /* Complex-image forward operator (for the adjoint identity): x_cplx N x N float2. */
 wproj_status wproj_phi_cplx(wproj_plan *p, const void *x_cplx, void *y, void *stream);
 

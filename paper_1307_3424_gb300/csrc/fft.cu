@@ -292,6 +292,26 @@ wproj_status phi_fwd_impl(wproj_plan *p, const float *x, const float2 *xc, float
   return WPROJ_OK;
 }
 
+// The same two passes with a caller-provided intermediate buffer (N x G float2).
+template <int LOGN>
+wproj_status phi_fwd_into_impl(wproj_plan *p, const float *x, float2 *inter, float2 *Xt, cudaStream_t s) {
+  const int N = p->g.N, G = p->g.G;
+  const float2 *tw = p->twiddle.as<float2>();
+  {
+    using Cfg = RowCfg<LOGN>;
+    WPROJ_TRY(set_smem(k_phi_fwd_rows<LOGN>, Cfg::SMEM));
+    k_phi_fwd_rows<LOGN><<<ceil_div(N, Cfg::C), Cfg::T, Cfg::SMEM, s>>>(x, nullptr, p->inv_a.as<float>(), N, inter, tw);
+    WPROJ_CHECK_LAUNCH("phi fwd rows");
+  }
+  {
+    using Cfg = ColCfg<LOGN>;
+    WPROJ_TRY(set_smem(k_phi_fwd_cols<LOGN>, Cfg::SMEM));
+    k_phi_fwd_cols<LOGN><<<ceil_div(G, Cfg::C), Cfg::T, Cfg::SMEM, s>>>(inter, N, Xt, 1.0f / G, tw);
+    WPROJ_CHECK_LAUNCH("phi fwd cols");
+  }
+  return WPROJ_OK;
+}
+
 template <int LOGN>
 wproj_status phi_adj_impl(wproj_plan *p, const float2 *Xt2, float *x_re, float2 *x_c, const float *z,
                           int mode, cudaStream_t s) {
@@ -368,6 +388,12 @@ wproj_status box_fft_impl(wproj_plan *p, const BoxBatch &bb, cudaStream_t s) {
   }
 
 }  // namespace
+
+wproj_status phi_forward_fft_into(wproj_plan *p, const float *x, float2 *inter, float2 *Xt, cudaStream_t s) {
+#define CALL(L) phi_fwd_into_impl<L>(p, x, inter, Xt, s)
+  WPROJ_LOGN_SWITCH(ilog2(p->g.G), CALL)
+#undef CALL
+}
 
 wproj_status init_twiddles(wproj_plan *p, cudaStream_t s) {
   WPROJ_TRY(p->twiddle.alloc(sizeof(float2) * kTwiddleLen));

@@ -196,6 +196,33 @@ wproj_status degrid(wproj_plan *p, const float2 *Xt, float2 *y, cudaStream_t s) 
   return WPROJ_OK;
 }
 
+// Degridding with a caller-provided buffer for the per-piece partial sums
+// (n_pieces float2); the kernels and their launch shape are those of degrid().
+wproj_status degrid_into(wproj_plan *p, const float2 *Xt, float2 *partial, float2 *y, cudaStream_t s) {
+  const int blocks = (int)std::min<int64_t>(ceil_div(p->n_pieces * 32, 256), 152 * 16);
+  switch (p->g.value_dtype) {
+    case WPROJ_VAL_F32:
+      k_degrid<WPROJ_VAL_F32><<<blocks, 256, 0, s>>>(p->n_pieces, p->piece_row.as<int32_t>(), p->piece_lo.as<int64_t>(),
+                                                     p->piece_len.as<int32_t>(), p->col.as<int32_t>(), p->val.ptr, Xt,
+                                                     partial);
+      break;
+    case WPROJ_VAL_BF16:
+      k_degrid<WPROJ_VAL_BF16><<<blocks, 256, 0, s>>>(p->n_pieces, p->piece_row.as<int32_t>(), p->piece_lo.as<int64_t>(),
+                                                      p->piece_len.as<int32_t>(), p->col.as<int32_t>(), p->val.ptr, Xt,
+                                                      partial);
+      break;
+    default:
+      k_degrid<WPROJ_VAL_F16><<<blocks, 256, 0, s>>>(p->n_pieces, p->piece_row.as<int32_t>(), p->piece_lo.as<int64_t>(),
+                                                     p->piece_len.as<int32_t>(), p->col.as<int32_t>(), p->val.ptr, Xt,
+                                                     partial);
+  }
+  WPROJ_CHECK_LAUNCH("degrid");
+  k_degrid_reduce<<<ceil_div(p->m, 256), 256, 0, s>>>(p->m, p->row_piece_ptr.as<int32_t>(), partial,
+                                                      p->g.value_dtype == WPROJ_VAL_F32 ? nullptr : p->row_scale.as<float>(), y);
+  WPROJ_CHECK_LAUNCH("degrid reduce");
+  return WPROJ_OK;
+}
+
 wproj_status grid(wproj_plan *p, const float2 *y, float2 *Xt2, cudaStream_t s) {
   p->launches += 2;
   const GridGeom &g = p->g;

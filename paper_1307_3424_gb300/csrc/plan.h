@@ -142,8 +142,11 @@ wproj_status fft2d_generic(const float2 *in, float2 *out, int n, int batch, int 
 struct BoxBatch;
 wproj_status box_fft(wproj_plan *p, const BoxBatch &bb, cudaStream_t s);
 
+wproj_status phi_forward_fft_into(wproj_plan *p, const float *x, float2 *inter, float2 *Xt, cudaStream_t s);
+
 // ops.cu
 wproj_status degrid(wproj_plan *p, const float2 *Xt, float2 *y, cudaStream_t s);
+wproj_status degrid_into(wproj_plan *p, const float2 *Xt, float2 *partial, float2 *y, cudaStream_t s);
 wproj_status grid(wproj_plan *p, const float2 *y, float2 *Xt2, cudaStream_t s);
 wproj_status apply_phi(wproj_plan *p, const float *x, const float2 *xc, float2 *y, cudaStream_t s);
 wproj_status apply_phi_adj(wproj_plan *p, const float2 *y, float *x_re, float2 *x_cplx,

@@ -27,7 +27,7 @@ EXPORTED = [
     "wproj_phi", "wproj_phi_adj", "wproj_phi_cplx", "wproj_solve_bpdn", "wproj_power_norm2",
     "wproj_fft2d", "wproj_set_timing", "wproj_get_stats", "wproj_reset_stats",
     "wproj_dr_defaults", "wproj_last_error", "wproj_version", "wproj_dr_state_get",
-    "wproj_dr_state_set",
+    "wproj_dr_state_set", "wproj_phi_noalloc",
 ]
 
 
@@ -99,6 +99,7 @@ def lib() -> ctypes.CDLL:
         "wproj_phi": [vp, vp, vp, vp],
         "wproj_phi_adj": [vp, vp, vp, vp, vp],
         "wproj_phi_cplx": [vp, vp, vp, vp],
+        "wproj_phi_noalloc": [vp, vp, vp, vp],
         "wproj_solve_bpdn": [vp, vp, dbl, P(DRParams), vp, P(SolveInfo), vp],
         "wproj_power_norm2": [vp, i32, P(dbl), vp],
         "wproj_fft2d": [vp, vp, i32, i32, i32, vp],
