@@ -272,6 +272,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     st = plan.stats()
+    csrv = plan.csr()
+    fmt, n_seg = csrv.index_format, csrv.n_seg
+    del csrv
     nnz, M, G = st["nnz"], st["m"], plan.G
 
     # data and solver state
@@ -343,11 +346,13 @@ def run_ours(args):
     grid_ms = kst["t_grid_ms"] / max(1, kst["n_grid"])
     alg_deg = nnz * b_val + M * 8 + G * G * 8
     alg_grid = nnz * b_val + M * 8 + G * G * 8
-    stored = nnz * (b_val + 4)
+    idx_bytes = nnz * 4 if fmt == "columns" else n_seg * 128
+    stored = nnz * b_val + idx_bytes
+    sfx = "_mask" if fmt == "mask" else ""
     if kst["t_degrid_ms"] >= kst["t_grid_ms"]:
-        dom, ms, alg, kname = "degrid", deg_ms, alg_deg, "k_degrid"
+        dom, ms, alg, kname = "degrid", deg_ms, alg_deg, "k_degrid" + sfx
     else:
-        dom, ms, alg, kname = "grid", grid_ms, alg_grid, "k_grid"
+        dom, ms, alg, kname = "grid", grid_ms, alg_grid, "k_grid" + sfx
     achieved = alg / (ms * 1e-3) / 1e9
     roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
             "frac": achieved / hbm_peak, "traffic": read_profile_traffic(kname),
@@ -370,7 +375,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(wl, e, {"nnz": nnz, "G_bytes": nnz * (b_val + 4),
+            "config": workload_config(wl, e, {"nnz": nnz, "G_bytes": stored, "index_format": fmt,
                                               "value_dtype": args.value_dtype,
                                               "l2": "inputs larger than L2 (G exceeds L2 many times)",
                                               "parallelism": f"replicas x{ws}"}),

@@ -77,7 +77,15 @@ typedef struct {
                            of two with 16 <= S <= G (S = G is exact) */
   int32_t value_dtype;  /* wproj_value_dtype of the stored G values; bf16/f16 values are
                            scaled per row by 1 / max|G[k,:]| (row_scale holds max|G[k,:]|) */
+  int32_t index_format; /* wproj_index_format: how the columns of G are stored */
 } wproj_grid_desc;
+
+/* Column storage of G.  Entries of a row are grouped by 32 x 32 grid tile (tiles
+ * ascending) and stored row-major inside a tile, so each (row, tile) segment can
+ * carry its columns either as int32 indices (4 B per entry) or as a 32-word bit
+ * mask of the tile (bit l of word r = cell (r, l) is stored; 128 B per segment).
+ * AUTO picks the mask when segments average >= 32 entries. */
+typedef enum { WPROJ_INDEX_AUTO = 0, WPROJ_INDEX_COLUMNS = 1, WPROJ_INDEX_TILE_MASK = 2 } wproj_index_format;
 
 /* View of G held by a plan (device pointers owned by the plan; valid until the
  * next build or the plan's destruction). */
@@ -86,12 +94,19 @@ typedef struct {
   int64_t nnz;              /* stored entries */
   int64_t n_cols;           /* G * G */
   const int64_t *row_ptr;   /* m + 1 offsets */
-  const int32_t *col;       /* nnz column indices; within a row grouped by 32x32 grid
-                               tile (tiles ascending), row-major inside a tile */
+  const int32_t *col;       /* nnz column indices (WPROJ_INDEX_COLUMNS), else NULL: use
+                               wproj_csr_columns to expand the tile masks */
   const void *val;          /* nnz complex values: float2, or (bf16, bf16) / (f16, f16) pairs */
   const float *row_scale;   /* m scales (bf16/f16), NULL for f32 */
   int32_t value_dtype;
+  int32_t index_format;     /* WPROJ_INDEX_COLUMNS or WPROJ_INDEX_TILE_MASK */
+  int64_t n_seg;            /* (row, tile) segments */
+  const uint32_t *tile_mask;  /* n_seg x 32 words (tile-mask format), else NULL */
 } wproj_csr;
+
+/* Column index of every stored entry of G (nnz int32, CSR order) written to
+ * col_out (device), whatever the index format. */
+wproj_status wproj_csr_columns(const wproj_plan *p, int32_t *col_out, void *stream);
 
 /* Douglas-Rachford parameters (the paper states none; these are the defaults
  * used by the oracle and the benchmarks). */

@@ -147,6 +147,7 @@ wproj_status wproj_plan_create(wproj_plan **out, const wproj_grid_desc *d) {
   if (d->box != 0 && (!is_pow2(d->box) || d->box < 16 || d->box > G))
     return fail(WPROJ_ERR_INVALID_ARG, "box must be 0 or a power of two in [16, 2N]");
   if (d->value_dtype < 0 || d->value_dtype > 2) return fail(WPROJ_ERR_INVALID_ARG, "value_dtype must be 0, 1 or 2");
+  if (d->index_format < 0 || d->index_format > 2) return fail(WPROJ_ERR_INVALID_ARG, "index_format must be 0, 1 or 2");
   const double lmax = d->extension == WPROJ_EXT_CLAMP ? 0.5 * d->fov : d->fov;
   if (d->chirp == WPROJ_CHIRP_EXACT && 2.0 * lmax * lmax >= 1.0)
     return fail(WPROJ_ERR_INVALID_ARG, "1 - l^2 - m^2 < 0 on the sampled box (fov too large)");
@@ -164,6 +165,7 @@ wproj_status wproj_plan_create(wproj_plan **out, const wproj_grid_desc *d) {
   g.extension = d->extension;
   g.box = d->box;
   g.value_dtype = d->value_dtype;
+  g.index_format = d->index_format;
   g.tile = G < kTile ? G : kTile;
   g.nT = G / g.tile;
   cudaGetDevice(&p->device);
@@ -223,6 +225,17 @@ wproj_status wproj_get_csr(const wproj_plan *p, wproj_csr *out) {
   out->val = p->val.ptr;
   out->row_scale = p->g.value_dtype == WPROJ_VAL_F32 ? nullptr : p->row_scale.as<float>();
   out->value_dtype = p->g.value_dtype;
+  out->index_format = p->fmt;
+  out->n_seg = p->n_seg;
+  out->col = p->fmt == WPROJ_INDEX_COLUMNS ? p->col.as<int32_t>() : nullptr;
+  out->tile_mask = p->fmt == WPROJ_INDEX_TILE_MASK ? p->seg_mask.as<uint32_t>() : nullptr;
+  return WPROJ_OK;
+}
+
+wproj_status wproj_csr_columns(const wproj_plan *p, int32_t *col_out, void *stream) {
+  WPROJ_TRY(check_built(p));
+  if (!col_out) return fail(WPROJ_ERR_INVALID_ARG, "null col_out");
+  return csr_columns(p, col_out, as_stream(stream));
   return WPROJ_OK;
 }
 

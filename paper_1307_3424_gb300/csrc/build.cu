@@ -41,6 +41,11 @@ constexpr int kSelChunk = 8192;          // entries per histogram block
 // fill the GPU and large ones keep the partial sums small.
 int64_t degrid_piece(int64_t nnz) { return std::min<int64_t>(16384, std::max<int64_t>(512, nnz / (152 * 64))); }
 int64_t grid_chunk(int64_t nnz) { return std::min<int64_t>(262144, std::max<int64_t>(4096, nnz / (152 * 16))); }
+// segments per degridding piece in the tile-mask format (about degrid_piece entries)
+int64_t seg_piece(int64_t nnz, int64_t n_seg) {
+  const int64_t avg = std::max<int64_t>(1, nnz / std::max<int64_t>(1, n_seg));
+  return std::min<int64_t>(4096, std::max<int64_t>(1, degrid_piece(nnz) / avg));
+}
 
 enum : int { ERR_NONFINITE = 1, ERR_BAND = 2, ERR_EMIT = 4 };
 
@@ -478,24 +483,10 @@ __global__ void k_tie_alloc(int nb, const int32_t *__restrict__ ids, const int64
 
 // ---- emission -------------------------------------------------------------------------
 
-__device__ __forceinline__ int block_excl_scan_int256(int v, int *tot, int *wt) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int inc = v;
-  for (int o = 1; o < 32; o <<= 1) {
-    int n = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += n;
-  }
-  if (lane == 31) wt[wid] = inc;
-  __syncthreads();
-  int off = 0, all = 0;
-  for (int i = 0; i < 8; ++i) { if (i < wid) off += wt[i]; all += wt[i]; }
-  __syncthreads();
-  *tot = all;
-  return off + inc - v;
-}
-
-// One block per (box, touched tile): 256 threads, 4 consecutive cells each of the
-// 32 x 32 tile in row-major order.
+// One block per (box, touched tile) segment.  Warp w handles tile rows 4w..4w+3,
+// lane = tile column, so a ballot is one row of the tile: the selection word of
+// the tile-mask format, and its popcount prefix gives each entry's place in the
+// row-major compacted order.  Ties are taken in the same row-major order.
 __global__ void __launch_bounds__(256)
 k_emit(const float2 *__restrict__ K, int S, const int32_t *__restrict__ ids,
        const int2 *__restrict__ j0, const int64_t *__restrict__ seg_base,
@@ -503,8 +494,10 @@ k_emit(const float2 *__restrict__ K, int S, const int32_t *__restrict__ ids,
        const int32_t *__restrict__ seg_tieb, const uint32_t *__restrict__ r_thr,
        const int32_t *__restrict__ r_ntie, const int8_t *__restrict__ r_all,
        const float *__restrict__ r_max, const int32_t *__restrict__ seg_cnt,
-       int32_t *__restrict__ col, void *__restrict__ val, int vdt, int *__restrict__ err) {
-  __shared__ int wt[8];
+       int32_t *__restrict__ col, uint32_t *__restrict__ mask, int fmt, void *__restrict__ val, int vdt,
+       int *__restrict__ err) {
+  __shared__ unsigned tiew[32], selw[32];
+  __shared__ int tiepre[32], selpre[33];
   const int b = blockIdx.y;
   const int k = ids[b];
   const int nt = ntile[k];
@@ -516,56 +509,76 @@ k_emit(const float2 *__restrict__ K, int S, const int32_t *__restrict__ ids,
   const bool all = r_all[k] != 0;
   const float inv_scale = (vdt != WPROJ_VAL_F32 && r_max[k] > 0.f) ? 1.0f / r_max[k] : 1.0f;
   const float2 *Kb = K + int64_t(b) * S * S;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
   for (int seg = blockIdx.x; seg < nt; seg += gridDim.x) {
     const int iu_t = seg / tv.nt, iv_t = seg % tv.nt;
     const int tile_u = axis_tile_at(tu, iu_t, g.nT), tile_v = axis_tile_at(tv, iv_t, g.nT);
     const int64_t sid = seg_base[k] + seg;
-    const int cells = TS * TS;
-    const int per = (cells + 255) / 256;   // 4 for 32x32 tiles
-    int cu_[4], cv_[4], kidx[4];
-    unsigned key[4];
-    bool inb[4];
-    int ties = 0;
-    for (int j = 0; j < per; ++j) {
-      const int cell = threadIdx.x * per + j;
-      inb[j] = false;
-      if (cell < cells) {
-        const int lu = cell / TS, lv = cell % TS;
-        const int cu = tile_u * TS + lu, cv = tile_v * TS + lv;
+    int kidx[4];
+    bool gt[4], eq[4];
+    for (int rr = 0; rr < 4; ++rr) {
+      const int r = 4 * w + rr;
+      gt[rr] = eq[rr] = false;
+      kidx[rr] = 0;
+      if (r < TS && lane < TS) {
+        const int cu = tile_u * TS + r, cv = tile_v * TS + lane;
         const int du = ((cu - tu.a) % g.G + g.G) % g.G;
         const int dv = ((cv - tv.a) % g.G + g.G) % g.G;
         if (du < S && dv < S) {
-          inb[j] = true;
-          cu_[j] = cu; cv_[j] = cv;
           const int iu = (du + S / 2) & (S - 1), iv = (dv + S / 2) & (S - 1);
-          kidx[j] = iu * S + iv;
-          key[j] = __float_as_uint(abs2_rn(Kb[kidx[j]]));
-          if (!all && key[j] == thr) ++ties;
+          kidx[rr] = iu * S + iv;
+          const unsigned key = __float_as_uint(abs2_rn(Kb[kidx[rr]]));
+          gt[rr] = all || key > thr;
+          eq[rr] = !all && key == thr;
         }
       }
+      const unsigned tw = __ballot_sync(0xffffffffu, eq[rr]);
+      if (lane == 0) tiew[r] = tw;
     }
-    int tot;
-    int trank = block_excl_scan_int256(ties, &tot, wt) + seg_tieb[sid];
+    __syncthreads();
+    if (w == 0) {
+      const int c = __popc(tiew[lane]);
+      int inc = c;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int n = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += n;
+      }
+      tiepre[lane] = inc - c;
+    }
+    __syncthreads();
+    const int tie0 = seg_tieb[sid];
     bool sel[4];
-    int nsel = 0;
-    for (int j = 0; j < per; ++j) {
-      sel[j] = false;
-      if (!inb[j]) continue;
-      if (all || key[j] > thr) sel[j] = true;
-      else if (key[j] == thr) { sel[j] = trank < ntie; ++trank; }
-      nsel += sel[j];
+    for (int rr = 0; rr < 4; ++rr) {
+      const int r = 4 * w + rr;
+      const int rank = tie0 + tiepre[r] + __popc(tiew[r] & lt);
+      sel[rr] = gt[rr] || (eq[rr] && rank < ntie);
+      const unsigned sw = __ballot_sync(0xffffffffu, sel[rr]);
+      if (lane == 0) selw[r] = sw;
     }
-    int pos = block_excl_scan_int256(nsel, &tot, wt);
+    __syncthreads();
+    if (w == 0) {
+      const int c = __popc(selw[lane]);
+      int inc = c;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int n = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += n;
+      }
+      selpre[lane] = inc - c;
+      if (lane == 31) selpre[32] = inc;
+    }
+    __syncthreads();
     const int64_t o = seg_off[sid];
     const int cnt = seg_cnt[sid];
-    if (threadIdx.x == 0 && tot != cnt) atomicOr(err, ERR_EMIT);
-    for (int j = 0; j < per; ++j) {
-      if (!sel[j]) continue;
-      if (pos >= cnt) break;      // never taken when the two passes agree
+    if (threadIdx.x == 0 && selpre[32] != cnt) atomicOr(err, ERR_EMIT);
+    for (int rr = 0; rr < 4; ++rr) {
+      if (!sel[rr]) continue;
+      const int r = 4 * w + rr;
+      const int pos = selpre[r] + __popc(selw[r] & lt);
+      if (pos >= cnt) continue;      // never taken when the two passes agree
       const int64_t at = o + pos;
-      ++pos;
-      col[at] = cu_[j] * g.G + cv_[j];
-      const float2 v = Kb[kidx[j]];
+      if (fmt == WPROJ_INDEX_COLUMNS) col[at] = (tile_u * TS + r) * g.G + tile_v * TS + lane;
+      const float2 v = Kb[kidx[rr]];
       if (vdt == WPROJ_VAL_F32) {
         reinterpret_cast<float2 *>(val)[at] = v;
       } else if (vdt == WPROJ_VAL_BF16) {
@@ -574,14 +587,15 @@ k_emit(const float2 *__restrict__ K, int S, const int32_t *__restrict__ ids,
         reinterpret_cast<__half2 *>(val)[at] = __floats2half2_rn(v.x * inv_scale, v.y * inv_scale);
       }
     }
+    if (fmt == WPROJ_INDEX_TILE_MASK && w == 0) mask[sid * 32 + lane] = selw[lane];
     __syncthreads();
   }
 }
 
 __global__ void k_row_ptr(int64_t m, const int64_t *__restrict__ seg_base,
                           const int64_t *__restrict__ seg_off, const int32_t *__restrict__ ntile,
-                          int64_t n_seg, int64_t nnz, int64_t piece, int64_t *__restrict__ row_ptr,
-                          int32_t *__restrict__ npieces) {
+                          int64_t n_seg, int64_t nnz, int64_t piece, int fmt, int64_t seg_piece,
+                          int64_t *__restrict__ row_ptr, int32_t *__restrict__ npieces) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k > m) return;
   if (k == m) { row_ptr[m] = nnz; return; }
@@ -589,26 +603,38 @@ __global__ void k_row_ptr(int64_t m, const int64_t *__restrict__ seg_base,
   const int64_t start = (sb < n_seg) ? seg_off[sb] : nnz;
   const int64_t end = (k + 1 < m) ? ((seg_base[k + 1] < n_seg) ? seg_off[seg_base[k + 1]] : nnz) : nnz;
   row_ptr[k] = start;
-  const int64_t n = end - start;
-  npieces[k] = int32_t(i64max(1, (n + piece - 1) / piece));
-  (void)ntile;
+  if (fmt == WPROJ_INDEX_TILE_MASK) {
+    npieces[k] = int32_t(i64max(1, (ntile[k] + seg_piece - 1) / seg_piece));
+  } else {
+    const int64_t n = end - start;
+    npieces[k] = int32_t(i64max(1, (n + piece - 1) / piece));
+  }
 }
 
+// Row pieces of the degridding: ranges of entries (column format) or of
+// segments (tile-mask format).
 __global__ void k_pieces(int64_t m, const int64_t *__restrict__ row_ptr,
                          const int64_t *__restrict__ piece_base, int32_t *__restrict__ piece_row,
                          int64_t *__restrict__ piece_lo, int32_t *__restrict__ piece_len,
-                         int32_t *__restrict__ row_piece_ptr, int64_t n_pieces, int64_t piece) {
+                         int32_t *__restrict__ row_piece_ptr, int64_t n_pieces, int64_t piece, int fmt,
+                         int64_t seg_piece, const int64_t *__restrict__ seg_base,
+                         const int32_t *__restrict__ ntile) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k > m) return;
   if (k == m) { row_piece_ptr[m] = int32_t(n_pieces); return; }
-  const int64_t lo = row_ptr[k], hi = row_ptr[k + 1];
   const int64_t pb = piece_base[k];
   row_piece_ptr[k] = int32_t(pb);
-  const int np = int(i64max(1, (hi - lo + piece - 1) / piece));
+  int64_t lo, n, step;
+  if (fmt == WPROJ_INDEX_TILE_MASK) {
+    lo = seg_base[k]; n = ntile[k]; step = seg_piece;
+  } else {
+    lo = row_ptr[k]; n = row_ptr[k + 1] - lo; step = piece;
+  }
+  const int np = int(i64max(1, (n + step - 1) / step));
   for (int i = 0; i < np; ++i) {
     piece_row[pb + i] = int32_t(k);
-    piece_lo[pb + i] = lo + int64_t(i) * piece;
-    piece_len[pb + i] = int32_t(i64min(piece, hi - lo - int64_t(i) * piece));
+    piece_lo[pb + i] = lo + int64_t(i) * step;
+    piece_len[pb + i] = int32_t(i64max(0, i64min(step, n - int64_t(i) * step)));
   }
 }
 
@@ -616,7 +642,7 @@ __global__ void k_pieces(int64_t m, const int64_t *__restrict__ row_ptr,
 __global__ void k_gather_cnt(int64_t n, const int32_t *__restrict__ tile_seg,
                              const int32_t *__restrict__ seg_cnt, const int64_t *__restrict__ seg_off,
                              const int32_t *__restrict__ seg_row, int32_t *__restrict__ out,
-                             SegMeta *__restrict__ meta) {
+                             SegMeta *__restrict__ meta, int fmt) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int sg = tile_seg[i];
@@ -624,7 +650,7 @@ __global__ void k_gather_cnt(int64_t n, const int32_t *__restrict__ tile_seg,
   out[i] = c;
   SegMeta m;
   m.off = seg_off[sg];
-  m.cnt = c;
+  m.aux = (fmt == WPROJ_INDEX_TILE_MASK) ? sg : c;
   m.row = seg_row[sg];
   meta[i] = m;
 }
@@ -716,15 +742,15 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
   WPROJ_TRY(p->seg_off.alloc(sizeof(int64_t) * std::max<int64_t>(1, n_seg)));
   WPROJ_TRY(p->seg_cnt.alloc(sizeof(int32_t) * std::max<int64_t>(1, n_seg)));
   WPROJ_TRY(p->seg_row.alloc(sizeof(int32_t) * std::max<int64_t>(1, n_seg)));
-  DevBuf d_segtile, d_cntgt, d_cnteq, d_tieb;
-  WPROJ_TRY(d_segtile.alloc(sizeof(int32_t) * std::max<int64_t>(1, n_seg)));
+  DevBuf d_cntgt, d_cnteq, d_tieb;
+  WPROJ_TRY(p->seg_tile.alloc(sizeof(int32_t) * std::max<int64_t>(1, n_seg)));
   WPROJ_TRY(d_cntgt.alloc(sizeof(int32_t) * std::max<int64_t>(1, n_seg)));
   WPROJ_TRY(d_cnteq.alloc(sizeof(int32_t) * std::max<int64_t>(1, n_seg)));
   WPROJ_TRY(d_tieb.alloc(sizeof(int32_t) * std::max<int64_t>(1, n_seg)));
   WPROJ_CUDA(cudaMemsetAsync(d_cntgt.ptr, 0, sizeof(int32_t) * n_seg, s));
   WPROJ_CUDA(cudaMemsetAsync(d_cnteq.ptr, 0, sizeof(int32_t) * n_seg, s));
   k_seg_fill<<<(unsigned)m, 128, 0, s>>>(m, g, d_j0.as<int2>(), d_Sk.as<int32_t>(), d_segbase.as<int64_t>(),
-                                         p->seg_row.as<int32_t>(), d_segtile.as<int32_t>());
+                                         p->seg_row.as<int32_t>(), p->seg_tile.as<int32_t>());
   WPROJ_CHECK_LAUNCH("seg fill");
 
   // ---- group rows by box size (stable: rows ascending inside a group)
@@ -782,13 +808,26 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
         WPROJ_CUDA(cudaMemcpy(&lc, p->seg_cnt.as<int32_t>() + (n_seg - 1), sizeof(int32_t), cudaMemcpyDeviceToHost));
       }
       p->nnz = lo + lc;
-      WPROJ_TRY(p->col.alloc(sizeof(int32_t) * std::max<int64_t>(1, p->nnz)));
+      // column storage: a 128-byte tile mask per segment beats 4-byte indices once
+      // segments average 32 entries
+      int fmt = g.index_format;
+      if (fmt == WPROJ_INDEX_AUTO) fmt = (p->nnz >= 32 * n_seg) ? WPROJ_INDEX_TILE_MASK : WPROJ_INDEX_COLUMNS;
+      if (g.tile != 32) fmt = WPROJ_INDEX_COLUMNS;
+      p->fmt = fmt;
+      if (fmt == WPROJ_INDEX_TILE_MASK) {
+        p->col.release();
+        WPROJ_TRY(p->seg_mask.alloc(sizeof(uint32_t) * 32 * std::max<int64_t>(1, n_seg)));
+      } else {
+        p->seg_mask.release();
+        WPROJ_TRY(p->col.alloc(sizeof(int32_t) * std::max<int64_t>(1, p->nnz)));
+      }
       WPROJ_TRY(p->val.alloc((vdt == WPROJ_VAL_F32 ? 8 : 4) * std::max<int64_t>(1, p->nnz)));
       WPROJ_TRY(p->row_ptr.alloc(sizeof(int64_t) * (m + 1)));
       WPROJ_TRY(d_pieces_n.alloc(sizeof(int32_t) * (m + 1)));
       k_row_ptr<<<ceil_div(m + 1, 256), 256, 0, s>>>(m, d_segbase.as<int64_t>(), p->seg_off.as<int64_t>(),
                                                      d_ntile.as<int32_t>(), n_seg, p->nnz, degrid_piece(p->nnz),
-                                                     p->row_ptr.as<int64_t>(), d_pieces_n.as<int32_t>());
+                                                     p->fmt, seg_piece(p->nnz, n_seg), p->row_ptr.as<int64_t>(),
+                                                     d_pieces_n.as<int32_t>());
       WPROJ_CHECK_LAUNCH("row ptr");
     }
     for (int c = 0; c < 9; ++c) {
@@ -851,7 +890,8 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
                                               d_ntile.as<int32_t>(), g, p->seg_off.as<int64_t>(),
                                               d_tieb.as<int32_t>(), r_thr.as<uint32_t>(), r_ntie.as<int32_t>(),
                                               r_all.as<int8_t>(), r_max.as<float>(), p->seg_cnt.as<int32_t>(),
-                                              p->col.as<int32_t>(), p->val.ptr, vdt, d_err.as<int>());
+                                              p->col.as<int32_t>(), p->seg_mask.as<uint32_t>(), p->fmt,
+                                              p->val.ptr, vdt, d_err.as<int>());
           WPROJ_CHECK_LAUNCH("emit");
         }
       }
@@ -883,7 +923,9 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
     k_pieces<<<ceil_div(m + 1, 256), 256, 0, s>>>(m, p->row_ptr.as<int64_t>(), pbase.as<int64_t>(),
                                                   p->piece_row.as<int32_t>(), p->piece_lo.as<int64_t>(),
                                                   p->piece_len.as<int32_t>(), p->row_piece_ptr.as<int32_t>(),
-                                                  p->n_pieces, degrid_piece(p->nnz));
+                                                  p->n_pieces, degrid_piece(p->nnz), p->fmt,
+                                                  seg_piece(p->nnz, n_seg), d_segbase.as<int64_t>(),
+                                                  d_ntile.as<int32_t>());
     WPROJ_CHECK_LAUNCH("pieces");
   }
 
@@ -893,7 +935,7 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
     DevBuf tptr, cntsorted, cum, nch, chbase;
     WPROJ_TRY(p->tile_seg.alloc(sizeof(int32_t) * std::max<int64_t>(1, n_seg)));
     WPROJ_TRY(tptr.alloc(sizeof(int64_t) * (n_tiles + 1)));
-    WPROJ_TRY(stable_bin_sort(d_segtile.as<int32_t>(), n_seg, n_tiles, p->tile_seg.as<int32_t>(),
+    WPROJ_TRY(stable_bin_sort(p->seg_tile.as<int32_t>(), n_seg, n_tiles, p->tile_seg.as<int32_t>(),
                               tptr.as<int64_t>(), s));
     WPROJ_TRY(cntsorted.alloc(sizeof(int32_t) * std::max<int64_t>(1, n_seg)));
     WPROJ_TRY(cum.alloc(sizeof(int64_t) * std::max<int64_t>(1, n_seg)));
@@ -901,7 +943,7 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
     if (n_seg > 0) {
       k_gather_cnt<<<ceil_div(n_seg, 256), 256, 0, s>>>(n_seg, p->tile_seg.as<int32_t>(), p->seg_cnt.as<int32_t>(),
                                                         p->seg_off.as<int64_t>(), p->seg_row.as<int32_t>(),
-                                                        cntsorted.as<int32_t>(), p->seg_meta.as<SegMeta>());
+                                                        cntsorted.as<int32_t>(), p->seg_meta.as<SegMeta>(), p->fmt);
       WPROJ_CHECK_LAUNCH("gather cnt");
       WPROJ_TRY(exclusive_scan_i32_to_i64(cntsorted.as<int32_t>(), cum.as<int64_t>(), n_seg, s));
     }

@@ -32,7 +32,7 @@ struct DevBuf {
 // of row `row`, all inside one grid tile.
 struct __align__(16) SegMeta {
   long long off;
-  int cnt;
+  int aux;      // entry count (column format) or segment id (tile-mask format)
   int row;
 };
 
@@ -54,6 +54,7 @@ struct GridGeom {
   double L, du, B, beta;
   int chirp, extension, box;
   int value_dtype;
+  int index_format;   // requested wproj_index_format
   int nT;        // tiles per axis = G / tile
   int tile;      // tile side (min(32, G))
 };
@@ -76,6 +77,9 @@ struct wproj_plan {
   wproj::DevBuf col;         // int32[nnz]
   wproj::DevBuf val;         // float2 or 2x16-bit [nnz]
   wproj::DevBuf row_scale;   // float[m]
+  int fmt = WPROJ_INDEX_COLUMNS;   // index format of the built G
+  wproj::DevBuf seg_mask;    // uint32[n_seg * 32] (tile-mask format)
+  wproj::DevBuf seg_tile;    // int32[n_seg] tile index of each segment
 
   // segments: one per (row, touched tile), ordered by row then tile
   int64_t n_seg = 0;
@@ -90,11 +94,11 @@ struct wproj_plan {
   wproj::DevBuf chunk_lo;    // int64[n_chunks]  positions in tile_seg
   wproj::DevBuf chunk_hi;    // int64[n_chunks]
   wproj::DevBuf tile_chunk_ptr;  // int32[nT*nT+1]
-  // degridding pieces
+  // degridding pieces: column format -> entry ranges; tile-mask format -> segment ranges
   int64_t n_pieces = 0;
   wproj::DevBuf piece_row;   // int32[n_pieces]
-  wproj::DevBuf piece_lo;    // int64[n_pieces]
-  wproj::DevBuf piece_len;   // int32[n_pieces]
+  wproj::DevBuf piece_lo;    // int64[n_pieces]  first entry / first segment
+  wproj::DevBuf piece_len;   // int32[n_pieces]  entries / segments
   wproj::DevBuf row_piece_ptr;   // int32[m+1]
 
   // work buffers
@@ -147,6 +151,7 @@ wproj_status phi_forward_fft_into(wproj_plan *p, const float *x, float2 *inter, 
 // ops.cu
 wproj_status degrid(wproj_plan *p, const float2 *Xt, float2 *y, cudaStream_t s);
 wproj_status degrid_into(wproj_plan *p, const float2 *Xt, float2 *partial, float2 *y, cudaStream_t s);
+wproj_status csr_columns(const wproj_plan *p, int32_t *col_out, cudaStream_t s);
 wproj_status grid(wproj_plan *p, const float2 *y, float2 *Xt2, cudaStream_t s);
 wproj_status apply_phi(wproj_plan *p, const float *x, const float2 *xc, float2 *y, cudaStream_t s);
 wproj_status apply_phi_adj(wproj_plan *p, const float2 *y, float *x_re, float2 *x_cplx,

@@ -21,13 +21,14 @@ OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NOT_BUILT, ERR_UNSUPPOR
 CHIRP = {"exact": 0, "linear": 1}
 EXTENSION = {"full": 0, "clamp": 1}
 VALUE_DTYPE = {"f32": 0, "bf16": 1, "f16": 2}
+INDEX_FORMAT = {"auto": 0, "columns": 1, "mask": 2}
 
 EXPORTED = [
     "wproj_plan_create", "wproj_plan_destroy", "wproj_build_kernels", "wproj_get_csr",
     "wproj_phi", "wproj_phi_adj", "wproj_phi_cplx", "wproj_solve_bpdn", "wproj_power_norm2",
     "wproj_fft2d", "wproj_set_timing", "wproj_get_stats", "wproj_reset_stats",
     "wproj_dr_defaults", "wproj_last_error", "wproj_version", "wproj_dr_state_get",
-    "wproj_dr_state_set", "wproj_phi_noalloc",
+    "wproj_dr_state_set", "wproj_phi_noalloc", "wproj_csr_columns",
 ]
 
 
@@ -40,13 +41,14 @@ class WprojError(RuntimeError):
 class GridDesc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("kb_support", ctypes.c_int32), ("fov", ctypes.c_double),
                 ("chirp", ctypes.c_int32), ("extension", ctypes.c_int32), ("box", ctypes.c_int32),
-                ("value_dtype", ctypes.c_int32)]
+                ("value_dtype", ctypes.c_int32), ("index_format", ctypes.c_int32)]
 
 
 class CSR(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int64), ("nnz", ctypes.c_int64), ("n_cols", ctypes.c_int64),
                 ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("val", ctypes.c_void_p),
-                ("row_scale", ctypes.c_void_p), ("value_dtype", ctypes.c_int32)]
+                ("row_scale", ctypes.c_void_p), ("value_dtype", ctypes.c_int32),
+                ("index_format", ctypes.c_int32), ("n_seg", ctypes.c_int64), ("tile_mask", ctypes.c_void_p)]
 
 
 class DRParams(ctypes.Structure):
@@ -100,6 +102,7 @@ def lib() -> ctypes.CDLL:
         "wproj_phi_adj": [vp, vp, vp, vp, vp],
         "wproj_phi_cplx": [vp, vp, vp, vp],
         "wproj_phi_noalloc": [vp, vp, vp, vp],
+        "wproj_csr_columns": [vp, vp, vp],
         "wproj_solve_bpdn": [vp, vp, dbl, P(DRParams), vp, P(SolveInfo), vp],
         "wproj_power_norm2": [vp, i32, P(dbl), vp],
         "wproj_fft2d": [vp, vp, i32, i32, i32, vp],
@@ -165,13 +168,15 @@ class CSRView:
     val: torch.Tensor          # complex64 (f32) or (nnz, 2) bf16/f16
     row_scale: torch.Tensor | None
     value_dtype: str
+    index_format: str = "columns"
+    n_seg: int = 0
 
 
 class Plan:
     """A libwproj plan: geometry, the built G and its work buffers."""
 
     def __init__(self, n: int, fov: float, kb_support: int = 4, chirp: str = "exact",
-                 extension: str = "full", box="G", value_dtype: str = "f32"):
+                 extension: str = "full", box="G", value_dtype: str = "f32", index_format: str = "auto"):
         """box: "G" (default) the exact S = 2N box, "rule" the S(w) rule, or a
         fixed power of two."""
         self._h = ctypes.c_void_p()
@@ -180,7 +185,7 @@ class Plan:
         self.value_dtype = value_dtype
         box_i = 2 * n if box in ("G", None) else (0 if box == "rule" else int(box))
         d = GridDesc(n, kb_support, float(fov), CHIRP[chirp], EXTENSION[extension], box_i,
-                     VALUE_DTYPE[value_dtype])
+                     VALUE_DTYPE[value_dtype], INDEX_FORMAT[index_format])
         self.desc = d
         self.m = 0
         _check(lib().wproj_plan_create(ctypes.byref(self._h), ctypes.byref(d)))
@@ -217,7 +222,11 @@ class Plan:
         dev = torch.device("cuda", torch.cuda.current_device())
         rp = torch.as_tensor(_CAI(c.row_ptr, (c.m + 1,), "<i8"), device=dev)
         nnz = max(int(c.nnz), 0)
-        col = torch.as_tensor(_CAI(c.col, (nnz,), "<i4"), device=dev)
+        if c.index_format == INDEX_FORMAT["columns"]:
+            col = torch.as_tensor(_CAI(c.col, (nnz,), "<i4"), device=dev)
+        else:   # tile masks: expand to a fresh column array
+            col = torch.empty(max(nnz, 1), dtype=torch.int32, device=dev)[:nnz]
+            _check(lib().wproj_csr_columns(self._h, ctypes.c_void_p(col.data_ptr()), _stream(None)))
         if c.value_dtype == 0:
             val = torch.as_tensor(_CAI(c.val, (nnz, 2), "<f4"), device=dev)
             val = torch.view_as_complex(val)
@@ -227,7 +236,8 @@ class Plan:
             val = val.view(torch.bfloat16 if c.value_dtype == 1 else torch.float16)
             rs = torch.as_tensor(_CAI(c.row_scale, (c.m,), "<f4"), device=dev)
         name = {0: "f32", 1: "bf16", 2: "f16"}[c.value_dtype]
-        return CSRView(int(c.m), int(c.nnz), int(c.n_cols), rp, col, val, rs, name)
+        fmt = {1: "columns", 2: "mask"}[c.index_format]
+        return CSRView(int(c.m), int(c.nnz), int(c.n_cols), rp, col, val, rs, name, fmt, int(c.n_seg))
 
     # ---- Part II
     def phi(self, x: torch.Tensor, y: torch.Tensor | None = None, stream=None) -> torch.Tensor:
