@@ -142,6 +142,9 @@ typedef struct {
   double t_fft_ms, t_degrid_ms, t_grid_ms, t_reduce_ms, t_solver_ms;
   int64_t n_fft, n_degrid, n_grid, n_reduce, n_solver;
   int64_t launches;          /* kernels launched by Phi, Phi^H and the solver since the last reset */
+  int32_t device_errors;     /* error bits raised on the device since the plan was created:
+                                1 = a staged copy of G did not arrive within ~1 s (the block
+                                gave up; results of that call are invalid) */
 } wproj_stats;
 
 /* ---- plan ---------------------------------------------------------------- */

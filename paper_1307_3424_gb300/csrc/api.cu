@@ -178,6 +178,9 @@ wproj_status wproj_plan_create(wproj_plan **out, const wproj_grid_desc *d) {
   chk(p->Xt2.alloc(sizeof(float2) * size_t(G) * G));
   chk(p->inter.alloc(sizeof(float2) * size_t(g.N) * G));
   chk(p->xtmp.alloc(sizeof(float) * size_t(g.N) * g.N));
+  chk(p->dev_err.alloc(sizeof(int)));
+  if (st == WPROJ_OK && cudaMemset(p->dev_err.ptr, 0, sizeof(int)) != cudaSuccess)
+    st = fail(WPROJ_ERR_CUDA, "plan init: memset");
   if (st == WPROJ_OK) {
     k_inv_a<<<ceil_div(g.N, 256), 256, 0, s>>>(g.N, g.W, g.beta, p->inv_a.as<float>());
     cudaError_t err = cudaGetLastError();
@@ -347,6 +350,9 @@ wproj_status wproj_get_stats(wproj_plan *p, wproj_stats *out) {
   out->n_reduce = p->timer.count[TC_REDUCE];
   out->n_solver = p->timer.count[TC_SOLVER];
   out->launches = p->launches;
+  int e = 0;
+  WPROJ_CUDA(cudaMemcpy(&e, p->dev_err.ptr, sizeof(int), cudaMemcpyDeviceToHost));
+  out->device_errors = e;
   return WPROJ_OK;
 }
 

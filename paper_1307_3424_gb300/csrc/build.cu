@@ -649,8 +649,9 @@ __global__ void k_gather_cnt(int64_t n, const int32_t *__restrict__ tile_seg,
   const int c = seg_cnt[sg];
   out[i] = c;
   SegMeta m;
-  m.off = seg_off[sg];
-  m.aux = (fmt == WPROJ_INDEX_TILE_MASK) ? sg : c;
+  m.off_cnt = (unsigned long long)seg_off[sg] | ((unsigned long long)c << 40);
+  m.seg = sg;
+  (void)fmt;
   m.row = seg_row[sg];
   meta[i] = m;
 }
@@ -821,7 +822,8 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
         p->seg_mask.release();
         WPROJ_TRY(p->col.alloc(sizeof(int32_t) * std::max<int64_t>(1, p->nnz)));
       }
-      WPROJ_TRY(p->val.alloc((vdt == WPROJ_VAL_F32 ? 8 : 4) * std::max<int64_t>(1, p->nnz)));
+      // 16 bytes of slack: staged copies widen each value run to 16-byte bounds
+      WPROJ_TRY(p->val.alloc((vdt == WPROJ_VAL_F32 ? 8 : 4) * std::max<int64_t>(1, p->nnz) + 16));
       WPROJ_TRY(p->row_ptr.alloc(sizeof(int64_t) * (m + 1)));
       WPROJ_TRY(d_pieces_n.alloc(sizeof(int32_t) * (m + 1)));
       k_row_ptr<<<ceil_div(m + 1, 256), 256, 0, s>>>(m, d_segbase.as<int64_t>(), p->seg_off.as<int64_t>(),
@@ -919,7 +921,8 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
     WPROJ_TRY(p->piece_lo.alloc(sizeof(int64_t) * p->n_pieces));
     WPROJ_TRY(p->piece_len.alloc(sizeof(int32_t) * p->n_pieces));
     WPROJ_TRY(p->row_piece_ptr.alloc(sizeof(int32_t) * (m + 1)));
-    WPROJ_TRY(p->piece_partial.alloc(sizeof(float2) * p->n_pieces));
+    WPROJ_TRY(p->piece_partial.alloc(sizeof(float2) *
+                                     std::max<int64_t>(1, p->fmt == WPROJ_INDEX_TILE_MASK ? 4 * n_seg : p->n_pieces)));
     k_pieces<<<ceil_div(m + 1, 256), 256, 0, s>>>(m, p->row_ptr.as<int64_t>(), pbase.as<int64_t>(),
                                                   p->piece_row.as<int32_t>(), p->piece_lo.as<int64_t>(),
                                                   p->piece_len.as<int32_t>(), p->row_piece_ptr.as<int32_t>(),
@@ -974,6 +977,10 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
   WPROJ_CUDA(cudaMemcpyAsync(&herr, d_err.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
   WPROJ_CUDA(cudaStreamSynchronize(s));
   if (herr & ERR_EMIT) return fail(WPROJ_ERR_CUDA, "build_kernels: emission pass disagrees with the counting pass");
+  // first segment of every row, closed by n_seg (per-row reduction of segment partials)
+  WPROJ_TRY(p->seg_base.alloc(sizeof(int64_t) * (m + 1)));
+  WPROJ_CUDA(cudaMemcpy(p->seg_base.ptr, d_segbase.ptr, sizeof(int64_t) * m, cudaMemcpyDeviceToDevice));
+  WPROJ_CUDA(cudaMemcpy(p->seg_base.as<int64_t>() + m, &n_seg, sizeof(int64_t), cudaMemcpyHostToDevice));
   p->m = m;
   p->n_seg = n_seg;
   p->built = true;

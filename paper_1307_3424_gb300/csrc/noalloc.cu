@@ -50,7 +50,7 @@ extern "C" wproj_status wproj_phi_noalloc(wproj_plan *p, const float *x, void *y
   if (!x || !y) return fail(WPROJ_ERR_INVALID_ARG, "null x or y");
   const size_t n_inter = round256(sizeof(float2) * size_t(p->g.N) * p->g.G);
   const size_t n_xt = round256(sizeof(float2) * size_t(p->g.G) * p->g.G);
-  const size_t n_part = round256(sizeof(float2) * size_t(p->n_pieces));
+  const size_t n_part = round256(sizeof(float2) * size_t(degrid_partials(p)));
   const size_t need = n_inter + n_xt + n_part;
   if (need > kNoAllocScratchBytes)
     return fail(WPROJ_ERR_INVALID_ARG, "phi_noalloc: this plan needs " + std::to_string(need) +

@@ -122,8 +122,8 @@ k_grid(const int32_t *__restrict__ chunk_tile, const int64_t *__restrict__ chunk
     if (more) nxt = meta[j + WARPS];
     float2 yk = __ldg(y + cur.row);
     if (row_scale) yk = cscale(yk, __ldg(row_scale + cur.row));
-    const int64_t off = cur.off;
-    const int n = cur.aux;
+    const int64_t off = meta_off(cur);
+    const int n = meta_cnt(cur);
     int i = lane;
     for (; i + 96 < n; i += 128) {
       const int q0 = __ldg(col + off + i), q1 = __ldg(col + off + i + 32);
@@ -180,134 +180,6 @@ __device__ __forceinline__ int warp_excl_scan(int v, int lane) {
   return inc - v;
 }
 
-// y partials: block (4 warps) per piece, a run of one row's segments.  Warp w
-// handles tile rows 8w..8w+7 of every segment, lane l column l: it gathers the
-// X values of its cells (coalesced 256-byte rows of X) and the stored values of
-// its rows with predicated loads, all 16 in flight before the first multiply.
-// The four warp sums are added in warp order at the end of the piece.
-constexpr int kDegridMaskWarps = 4;
-
-template <int VDT>
-__global__ void __launch_bounds__(kDegridMaskWarps * 32)
-k_degrid_mask(int64_t n_pieces, const int64_t *__restrict__ piece_seg, const int32_t *__restrict__ piece_nseg,
-              const int32_t *__restrict__ seg_tile, const int64_t *__restrict__ seg_off,
-              const uint32_t *__restrict__ mask, const void *__restrict__ val, const float2 *__restrict__ Xt,
-              int logG, int lognT, float2 *__restrict__ partial) {
-  constexpr int R = 32 / kDegridMaskWarps;
-  __shared__ float2 red[kDegridMaskWarps];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const unsigned lt = (1u << lane) - 1u;
-  const int nTm = (1 << lognT) - 1;
-  for (int64_t pc = blockIdx.x; pc < n_pieces; pc += gridDim.x) {
-    const int64_t s0 = piece_seg[pc];
-    const int ns = piece_nseg[pc];
-    float ax = 0.f, ay = 0.f, bx = 0.f, by = 0.f;
-    unsigned word = 0;
-    int tile = 0;
-    int64_t off = 0;
-    if (ns > 0) { word = __ldg(mask + s0 * 32 + lane); tile = __ldg(seg_tile + s0); off = __ldg(seg_off + s0); }
-    for (int64_t s = s0; s < s0 + ns; ++s) {
-      // next segment's descriptor in flight while this one streams
-      unsigned nword = 0;
-      int ntile_ = 0;
-      int64_t noff = 0;
-      const bool more = s + 1 < s0 + ns;
-      if (more) { nword = __ldg(mask + (s + 1) * 32 + lane); ntile_ = __ldg(seg_tile + s + 1); noff = __ldg(seg_off + s + 1); }
-      const int pre = warp_excl_scan(__popc(word), lane);
-      const float2 *xr = Xt + ((int64_t(tile >> lognT) << 5) << logG) + ((tile & nTm) << 5) + lane;
-      float2 v[R], x[R];
-#pragma unroll
-      for (int i = 0; i < R; ++i) {
-        const int r = R * w + i;
-        const unsigned wr = __shfl_sync(0xffffffffu, word, r);
-        const int pr = __shfl_sync(0xffffffffu, pre, r);
-        const bool bit = (wr >> lane) & 1u;
-        v[i] = bit ? load_val<VDT>(val, off + pr + __popc(wr & lt)) : make_float2(0.f, 0.f);
-        x[i] = __ldg(xr + (int64_t(r) << logG));
-      }
-#pragma unroll
-      for (int i = 0; i < R; i += 2) {
-        ax = fmaf(v[i].x, x[i].x, ax); ax = fmaf(-v[i].y, x[i].y, ax);
-        ay = fmaf(v[i].x, x[i].y, ay); ay = fmaf(v[i].y, x[i].x, ay);
-        bx = fmaf(v[i + 1].x, x[i + 1].x, bx); bx = fmaf(-v[i + 1].y, x[i + 1].y, bx);
-        by = fmaf(v[i + 1].x, x[i + 1].y, by); by = fmaf(v[i + 1].y, x[i + 1].x, by);
-      }
-      if (more) { word = nword; tile = ntile_; off = noff; }
-    }
-    ax += bx;
-    ay += by;
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-      ax += __shfl_xor_sync(0xffffffffu, ax, o);
-      ay += __shfl_xor_sync(0xffffffffu, ay, o);
-    }
-    if (lane == 0) red[w] = make_float2(ax, ay);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      float2 t = red[0];
-#pragma unroll
-      for (int i = 1; i < kDegridMaskWarps; ++i) t = cadd(t, red[i]);
-      partial[pc] = t;
-    }
-    __syncthreads();
-  }
-}
-
-// Gridding: block (4 warps) per chunk of one tile's segments; warp w owns tile
-// rows 8w..8w+7 and lane l column l, so every accumulator lives in registers and
-// no two threads ever touch the same cell.  Each warp walks all segments of the
-// chunk (the mask words come through L1) and reads only its rows' values.
-constexpr int kGridMaskWarps = 4;
-constexpr int kGridMaskRows = 32 / kGridMaskWarps;
-
-template <int VDT>
-__global__ void __launch_bounds__(kGridMaskWarps * 32)
-k_grid_mask(const int32_t *__restrict__ chunk_tile, const int64_t *__restrict__ chunk_lo,
-            const int64_t *__restrict__ chunk_hi, const SegMeta *__restrict__ meta,
-            const uint32_t *__restrict__ mask, const void *__restrict__ val,
-            const float *__restrict__ row_scale, const float2 *__restrict__ y, float2 *__restrict__ partial) {
-  constexpr int R = kGridMaskRows;
-  const int c = blockIdx.x;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const unsigned lt = (1u << lane) - 1u;
-  const int64_t lo = chunk_lo[c], hi = chunk_hi[c];
-  float2 acc[R];
-#pragma unroll
-  for (int rr = 0; rr < R; ++rr) acc[rr] = make_float2(0.f, 0.f);
-  SegMeta m = {};
-  unsigned word = 0;
-  if (lo < hi) { m = meta[lo]; word = __ldg(mask + int64_t(m.aux) * 32 + lane); }
-  for (int64_t j = lo; j < hi; ++j) {
-    SegMeta mn = {};
-    unsigned nword = 0;
-    const bool more = j + 1 < hi;
-    if (more) { mn = meta[j + 1]; nword = __ldg(mask + int64_t(mn.aux) * 32 + lane); }
-    float2 yk = __ldg(y + m.row);
-    if (row_scale) yk = cscale(yk, __ldg(row_scale + m.row));
-    const int pre = warp_excl_scan(__popc(word), lane);
-    float2 v[R];
-#pragma unroll
-    for (int rr = 0; rr < R; ++rr) {
-      const int r = R * w + rr;
-      const unsigned wr = __shfl_sync(0xffffffffu, word, r);
-      const int pr = __shfl_sync(0xffffffffu, pre, r);
-      const bool bit = (wr >> lane) & 1u;
-      v[rr] = bit ? load_val<VDT>(val, m.off + pr + __popc(wr & lt)) : make_float2(0.f, 0.f);
-    }
-#pragma unroll
-    for (int rr = 0; rr < R; ++rr) {
-      // conj(v) * y
-      acc[rr].x = fmaf(v[rr].x, yk.x, acc[rr].x); acc[rr].x = fmaf(v[rr].y, yk.y, acc[rr].x);
-      acc[rr].y = fmaf(v[rr].x, yk.y, acc[rr].y); acc[rr].y = fmaf(-v[rr].y, yk.x, acc[rr].y);
-    }
-    if (more) { m = mn; word = nword; }
-  }
-  float2 *out = partial + int64_t(c) * 1024;
-#pragma unroll
-  for (int rr = 0; rr < R; ++rr) out[(R * w + rr) * 32 + lane] = acc[rr];
-  (void)chunk_tile;
-}
-
 // Column index of every stored entry (tile-mask format), warp per segment.
 __global__ void k_expand_cols(int64_t n_seg, const int32_t *__restrict__ seg_tile,
                               const int64_t *__restrict__ seg_off, const uint32_t *__restrict__ mask,
@@ -330,27 +202,18 @@ __global__ void k_expand_cols(int64_t n_seg, const int32_t *__restrict__ seg_til
   }
 }
 
-// Degridding kernels for the plan's index format and value type; partial sums
-// per row piece go to `partial` (n_pieces float2).
-wproj_status launch_degrid(wproj_plan *p, const float2 *Xt, float2 *partial, cudaStream_t s) {
+// Column-format degridding kernels; partial sums per row piece into `partial`.
+wproj_status launch_degrid_cols(wproj_plan *p, const float2 *Xt, float2 *partial, cudaStream_t s) {
   const int blocks = (int)std::min<int64_t>(ceil_div(p->n_pieces * 32, 256), 152 * 16);
-  const int logG = ilog2(p->g.G), lognT = ilog2(p->g.nT);
-  const int mblocks = (int)std::max<int64_t>(1, std::min<int64_t>(p->n_pieces, 152 * 32));
 #define DEGRID_COLS(VDT)                                                                                     \
   k_degrid<VDT><<<blocks, 256, 0, s>>>(p->n_pieces, p->piece_row.as<int32_t>(), p->piece_lo.as<int64_t>(),  \
                                        p->piece_len.as<int32_t>(), p->col.as<int32_t>(), p->val.ptr, Xt, partial)
-#define DEGRID_MASK(VDT)                                                                                     \
-  k_degrid_mask<VDT><<<mblocks, kDegridMaskWarps * 32, 0, s>>>(p->n_pieces, p->piece_lo.as<int64_t>(), p->piece_len.as<int32_t>(), \
-                                            p->seg_tile.as<int32_t>(), p->seg_off.as<int64_t>(),              \
-                                            p->seg_mask.as<uint32_t>(), p->val.ptr, Xt, logG, lognT, partial)
-  const bool mask = p->fmt == WPROJ_INDEX_TILE_MASK;
   switch (p->g.value_dtype) {
-    case WPROJ_VAL_F32: if (mask) DEGRID_MASK(WPROJ_VAL_F32); else DEGRID_COLS(WPROJ_VAL_F32); break;
-    case WPROJ_VAL_BF16: if (mask) DEGRID_MASK(WPROJ_VAL_BF16); else DEGRID_COLS(WPROJ_VAL_BF16); break;
-    default: if (mask) DEGRID_MASK(WPROJ_VAL_F16); else DEGRID_COLS(WPROJ_VAL_F16);
+    case WPROJ_VAL_F32: DEGRID_COLS(WPROJ_VAL_F32); break;
+    case WPROJ_VAL_BF16: DEGRID_COLS(WPROJ_VAL_BF16); break;
+    default: DEGRID_COLS(WPROJ_VAL_F16);
   }
 #undef DEGRID_COLS
-#undef DEGRID_MASK
   WPROJ_CHECK_LAUNCH("degrid");
   return WPROJ_OK;
 }
@@ -359,25 +222,28 @@ wproj_status launch_degrid(wproj_plan *p, const float2 *Xt, float2 *partial, cud
 
 wproj_status degrid(wproj_plan *p, const float2 *Xt, float2 *y, cudaStream_t s) {
   p->launches += 2;
+  return degrid_into(p, Xt, p->piece_partial.as<float2>(), y, s);
+}
+
+// Degridding with a caller-provided buffer for the partial sums
+// (degrid_partials(p) float2); the kernels and their launch shape are those of
+// degrid().
+wproj_status degrid_into(wproj_plan *p, const float2 *Xt, float2 *partial, float2 *y, cudaStream_t s) {
   {
     ScopedTimer t(p, TC_DEGRID, s);
-    WPROJ_TRY(launch_degrid(p, Xt, p->piece_partial.as<float2>(), s));
+    if (p->fmt == WPROJ_INDEX_TILE_MASK) WPROJ_TRY(degrid_mask(p, Xt, partial, s));
+    else WPROJ_TRY(launch_degrid_cols(p, Xt, partial, s));
   }
   ScopedTimer t(p, TC_REDUCE, s);
-  k_degrid_reduce<<<ceil_div(p->m, 256), 256, 0, s>>>(p->m, p->row_piece_ptr.as<int32_t>(), p->piece_partial.as<float2>(),
+  if (p->fmt == WPROJ_INDEX_TILE_MASK) return degrid_mask_reduce(p, partial, y, s);
+  k_degrid_reduce<<<ceil_div(p->m, 256), 256, 0, s>>>(p->m, p->row_piece_ptr.as<int32_t>(), partial,
                                                       p->g.value_dtype == WPROJ_VAL_F32 ? nullptr : p->row_scale.as<float>(), y);
   WPROJ_CHECK_LAUNCH("degrid reduce");
   return WPROJ_OK;
 }
 
-// Degridding with a caller-provided buffer for the per-piece partial sums
-// (n_pieces float2); the kernels and their launch shape are those of degrid().
-wproj_status degrid_into(wproj_plan *p, const float2 *Xt, float2 *partial, float2 *y, cudaStream_t s) {
-  WPROJ_TRY(launch_degrid(p, Xt, partial, s));
-  k_degrid_reduce<<<ceil_div(p->m, 256), 256, 0, s>>>(p->m, p->row_piece_ptr.as<int32_t>(), partial,
-                                                      p->g.value_dtype == WPROJ_VAL_F32 ? nullptr : p->row_scale.as<float>(), y);
-  WPROJ_CHECK_LAUNCH("degrid reduce");
-  return WPROJ_OK;
+int64_t degrid_partials(const wproj_plan *p) {
+  return p->fmt == WPROJ_INDEX_TILE_MASK ? degrid_mask_partials(p) : p->n_pieces;
 }
 
 wproj_status grid(wproj_plan *p, const float2 *y, float2 *Xt2, cudaStream_t s) {
@@ -390,23 +256,20 @@ wproj_status grid(wproj_plan *p, const float2 *y, float2 *Xt2, cudaStream_t s) {
     ScopedTimer t(p, TC_GRID, s);
 #define LAUNCH_GRID(VDT)                                                                                    \
   do {                                                                                                      \
-    if (p->fmt == WPROJ_INDEX_TILE_MASK) {                                                                  \
-      k_grid_mask<VDT><<<(unsigned)p->n_chunks, kGridMaskWarps * 32, 0, s>>>(                               \
-          p->chunk_tile.as<int32_t>(), p->chunk_lo.as<int64_t>(), p->chunk_hi.as<int64_t>(),                \
-          p->seg_meta.as<SegMeta>(), p->seg_mask.as<uint32_t>(), p->val.ptr, rs, y,                         \
-          p->grid_partial.as<float2>());                                                                    \
-    } else {                                                                                                \
-      WPROJ_CUDA(cudaFuncSetAttribute(k_grid<VDT, kGridWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-      k_grid<VDT, kGridWarps><<<(unsigned)p->n_chunks, kGridWarps * 32, smem, s>>>(                         \
-          p->chunk_tile.as<int32_t>(), p->chunk_lo.as<int64_t>(), p->chunk_hi.as<int64_t>(),                \
-          p->seg_meta.as<SegMeta>(), p->col.as<int32_t>(), p->val.ptr, rs, y, logG, g.tile, g.nT,           \
-          p->grid_partial.as<float2>());                                                                    \
-    }                                                                                                       \
+    WPROJ_CUDA(cudaFuncSetAttribute(k_grid<VDT, kGridWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+    k_grid<VDT, kGridWarps><<<(unsigned)p->n_chunks, kGridWarps * 32, smem, s>>>(                           \
+        p->chunk_tile.as<int32_t>(), p->chunk_lo.as<int64_t>(), p->chunk_hi.as<int64_t>(),                  \
+        p->seg_meta.as<SegMeta>(), p->col.as<int32_t>(), p->val.ptr, rs, y, logG, g.tile, g.nT,             \
+        p->grid_partial.as<float2>());                                                                      \
   } while (0)
-    switch (g.value_dtype) {
-      case WPROJ_VAL_F32: LAUNCH_GRID(WPROJ_VAL_F32); break;
-      case WPROJ_VAL_BF16: LAUNCH_GRID(WPROJ_VAL_BF16); break;
-      default: LAUNCH_GRID(WPROJ_VAL_F16);
+    if (p->fmt == WPROJ_INDEX_TILE_MASK) {
+      WPROJ_TRY(grid_mask(p, y, s));
+    } else {
+      switch (g.value_dtype) {
+        case WPROJ_VAL_F32: LAUNCH_GRID(WPROJ_VAL_F32); break;
+        case WPROJ_VAL_BF16: LAUNCH_GRID(WPROJ_VAL_BF16); break;
+        default: LAUNCH_GRID(WPROJ_VAL_F16);
+      }
     }
 #undef LAUNCH_GRID
     WPROJ_CHECK_LAUNCH("grid");

@@ -31,10 +31,14 @@ struct DevBuf {
 // One (row, tile) segment of G as the gridding reads it: entries [off, off+cnt)
 // of row `row`, all inside one grid tile.
 struct __align__(16) SegMeta {
-  long long off;
-  int aux;      // entry count (column format) or segment id (tile-mask format)
+  unsigned long long off_cnt;   // first entry (low 40 bits) | entry count << 40
+  int seg;                      // segment id (row-major segment order)
   int row;
 };
+__host__ __device__ __forceinline__ long long meta_off(const SegMeta &m) {
+  return (long long)(m.off_cnt & ((1ull << 40) - 1));
+}
+__host__ __device__ __forceinline__ int meta_cnt(const SegMeta &m) { return (int)(m.off_cnt >> 40); }
 
 // Timing accumulator for one class of kernels.
 enum TimerClass { TC_FFT = 0, TC_DEGRID, TC_GRID, TC_REDUCE, TC_SOLVER, TC_COUNT };
@@ -80,6 +84,7 @@ struct wproj_plan {
   int fmt = WPROJ_INDEX_COLUMNS;   // index format of the built G
   wproj::DevBuf seg_mask;    // uint32[n_seg * 32] (tile-mask format)
   wproj::DevBuf seg_tile;    // int32[n_seg] tile index of each segment
+  wproj::DevBuf seg_base;    // int64[m+1] first segment of each row
 
   // segments: one per (row, touched tile), ordered by row then tile
   int64_t n_seg = 0;
@@ -106,7 +111,8 @@ struct wproj_plan {
   wproj::DevBuf Xt2;         // float2[G*G]  G^H y
   wproj::DevBuf inter;       // float2[N*G]  between FFT passes
   wproj::DevBuf grid_partial;    // float2[n_chunks * tile^2]
-  wproj::DevBuf piece_partial;   // float2[n_pieces]
+  wproj::DevBuf piece_partial;   // float2[degrid_partials]: per row piece (columns) or segment (mask)
+  wproj::DevBuf dev_err;     // int: error bits raised by kernels (bounded waits)
   wproj::DevBuf xtmp;        // float[N*N]
   wproj::DevBuf ytmp;        // float2[m]
   // solver buffers
@@ -152,6 +158,13 @@ wproj_status phi_forward_fft_into(wproj_plan *p, const float *x, float2 *inter, 
 wproj_status degrid(wproj_plan *p, const float2 *Xt, float2 *y, cudaStream_t s);
 wproj_status degrid_into(wproj_plan *p, const float2 *Xt, float2 *partial, float2 *y, cudaStream_t s);
 wproj_status csr_columns(const wproj_plan *p, int32_t *col_out, cudaStream_t s);
+int64_t degrid_partials(const wproj_plan *p);   // partial sums degridding needs
+
+// tiles.cu (tile-mask format)
+int64_t degrid_mask_partials(const wproj_plan *p);
+wproj_status degrid_mask(wproj_plan *p, const float2 *Xt, float2 *partial, cudaStream_t s);
+wproj_status degrid_mask_reduce(wproj_plan *p, const float2 *partial, float2 *y, cudaStream_t s);
+wproj_status grid_mask(wproj_plan *p, const float2 *y, cudaStream_t s);
 wproj_status grid(wproj_plan *p, const float2 *y, float2 *Xt2, cudaStream_t s);
 wproj_status apply_phi(wproj_plan *p, const float *x, const float2 *xc, float2 *y, cudaStream_t s);
 wproj_status apply_phi_adj(wproj_plan *p, const float2 *y, float *x_re, float2 *x_cplx,

@@ -73,7 +73,7 @@ class Stats(ctypes.Structure):
                 ("t_reduce_ms", ctypes.c_double), ("t_solver_ms", ctypes.c_double),
                 ("n_fft", ctypes.c_int64), ("n_degrid", ctypes.c_int64), ("n_grid", ctypes.c_int64),
                 ("n_reduce", ctypes.c_int64), ("n_solver", ctypes.c_int64),
-                ("launches", ctypes.c_int64)]
+                ("launches", ctypes.c_int64), ("device_errors", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
