@@ -348,11 +348,12 @@ def run_ours(args):
     alg_grid = nnz * b_val + M * 8 + G * G * 8
     idx_bytes = nnz * 4 if fmt == "columns" else n_seg * 128
     stored = nnz * b_val + idx_bytes
-    sfx = "_mask" if fmt == "mask" else ""
+    # kernel labels as in profiles/: k_tiles<VDT, degrid?> for the tile-mask format
+    deg_name, grid_name = ("k_tiles_degrid", "k_tiles_grid") if fmt == "mask" else ("k_degrid", "k_grid")
     if kst["t_degrid_ms"] >= kst["t_grid_ms"]:
-        dom, ms, alg, kname = "degrid", deg_ms, alg_deg, "k_degrid" + sfx
+        dom, ms, alg, kname = "degrid", deg_ms, alg_deg, deg_name
     else:
-        dom, ms, alg, kname = "grid", grid_ms, alg_grid, "k_grid" + sfx
+        dom, ms, alg, kname = "grid", grid_ms, alg_grid, grid_name
     achieved = alg / (ms * 1e-3) / 1e9
     roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
             "frac": achieved / hbm_peak, "traffic": read_profile_traffic(kname),
