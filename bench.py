@@ -52,13 +52,19 @@ def parse():
     ap.add_argument("--value-dtype", default="f32", choices=["f32", "bf16", "f16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-rows", type=int, default=64)
+    ap.add_argument("--workload", default="paper", choices=["paper", "precision"])
+    ap.add_argument("--index-format", default="auto", choices=["auto", "columns", "mask"])
     ap.add_argument("--n", type=int, default=None, help="image side of a smaller profiling case")
     ap.add_argument("--m", type=int, default=None, help="visibilities of a smaller profiling case")
     return ap.parse_args()
 
 
 def workload(args):
-    """The paper-scale workload, or a smaller case of the same recipe (profiling)."""
+    """The paper-scale workload, the precision-form workload (--workload
+    precision: N=1024, M=2^21, S(w) boxes), or a smaller case of the paper-scale
+    recipe (profiling)."""
+    if args.workload == "precision":
+        return synth.PRECISION
     wl = synth.PAPER_SCALE
     if args.n is None and args.m is None:
         return wl
@@ -79,7 +85,8 @@ def dist_env():
 def workload_config(wl, e, extra=None):
     cfg = {"workload": f"{wl.name}_e{e}", "N": wl.N, "G": 2 * wl.N, "M": wl.M, "e": e,
            "uv": f"{wl.uv} sigma={wl.sigma_uv}B", "wd_max": wl.wd_max, "kb_support": wl.W,
-           "box": 2 * wl.N, "chirp": "exact", "dr_inner_iters": INNER, "pairs_per_step": PAIRS_PER_STEP}
+           "box": 2 * wl.N if wl.box == "G" else "rule S(w)", "chirp": "exact", "dr_inner_iters": INNER,
+           "pairs_per_step": PAIRS_PER_STEP}
     if extra:
         cfg.update(extra)
     return cfg
@@ -261,7 +268,7 @@ def run_ours(args):
 
     prob = synth.make_problem(wl, seed=rank)
     noise, sigma_n = synth.draw_noise(prob)
-    plan = wproj.Plan(wl.N, prob.L, value_dtype=args.value_dtype)
+    plan = wproj.Plan(wl.N, prob.L, value_dtype=args.value_dtype, box=wl.box, index_format=args.index_format)
     uvw_d = torch.from_numpy(prob.uvw).to(dev)
 
     # build G (once untimed to load modules, then timed)

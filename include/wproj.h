@@ -84,7 +84,8 @@ typedef struct {
  * ascending) and stored row-major inside a tile, so each (row, tile) segment can
  * carry its columns either as int32 indices (4 B per entry) or as a 32-word bit
  * mask of the tile (bit l of word r = cell (r, l) is stored; 128 B per segment).
- * AUTO picks the mask when segments average >= 32 entries. */
+ * AUTO picks the mask when segments average >= 256 entries (dense rows), the
+ * indices otherwise. */
 typedef enum { WPROJ_INDEX_AUTO = 0, WPROJ_INDEX_COLUMNS = 1, WPROJ_INDEX_TILE_MASK = 2 } wproj_index_format;
 
 /* View of G held by a plan (device pointers owned by the plan; valid until the

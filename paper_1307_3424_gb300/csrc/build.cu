@@ -88,6 +88,14 @@ __host__ __device__ __forceinline__ int axis_tile_pos(const AxisTiles &t, int ti
   return (tile <= t.t1) ? tile : tile - t.t0 + t.t1 + 1;
 }
 
+// Upper bound of the tiles one S x S box touches: all of them when S = G, else
+// at most ceil(S/tile) + 1 per axis.
+int box_tiles(int S, const GridGeom &g) {
+  if (S >= g.G) return g.nT * g.nT;
+  const int per = std::min(g.nT, (S + g.tile - 1) / g.tile + 1);
+  return per * per;
+}
+
 __device__ __forceinline__ double kb_dev(double t, int W, double beta) {
   const double r = 2.0 * t / W;
   const double arg = 1.0 - r * r;
@@ -413,15 +421,15 @@ __global__ void __launch_bounds__(256)
 k_tile_count(const float2 *__restrict__ K, int S, const int32_t *__restrict__ ids,
              const int2 *__restrict__ j0, const int64_t *__restrict__ seg_base, GridGeom g,
              const SelState *__restrict__ sel, int32_t *__restrict__ cnt_gt,
-             int32_t *__restrict__ cnt_eq) {
-  extern __shared__ int32_t sc[];   // [2][ntile]
+             int32_t *__restrict__ cnt_eq, int smem_tiles) {
+  extern __shared__ int32_t sc[];   // [2][smem_tiles]
   const int b = blockIdx.y;
   const int k = ids[b];
   const SelState st = sel[b];
   const AxisTiles tu = axis_tiles(j0[k].x, S, g.G, g.tile);
   const AxisTiles tv = axis_tiles(j0[k].y, S, g.G, g.tile);
   const int nt = tu.nt * tv.nt;
-  const bool use_smem = nt <= 4096;
+  const bool use_smem = nt <= smem_tiles;   // else count straight into global memory
   int32_t *gt = use_smem ? sc : cnt_gt + seg_base[k];
   int32_t *eq = use_smem ? sc + nt : cnt_eq + seg_base[k];
   if (use_smem) {
@@ -809,10 +817,13 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
         WPROJ_CUDA(cudaMemcpy(&lc, p->seg_cnt.as<int32_t>() + (n_seg - 1), sizeof(int32_t), cudaMemcpyDeviceToHost));
       }
       p->nnz = lo + lc;
-      // column storage: a 128-byte tile mask per segment beats 4-byte indices once
-      // segments average 32 entries
+      // column storage: the tile masks pay off for dense segments (they cut 4 of
+      // 12 bytes per entry), the column indices for sparse ones (the mask kernels
+      // spend per-segment work on all 32 tile rows); measured at N=256/M=32768
+      // (573 entries per segment: masks 1.5x faster) and N=1024/M=2^21 (41 per
+      // segment: columns 5x faster)
       int fmt = g.index_format;
-      if (fmt == WPROJ_INDEX_AUTO) fmt = (p->nnz >= 32 * n_seg) ? WPROJ_INDEX_TILE_MASK : WPROJ_INDEX_COLUMNS;
+      if (fmt == WPROJ_INDEX_AUTO) fmt = (p->nnz >= 256 * n_seg) ? WPROJ_INDEX_TILE_MASK : WPROJ_INDEX_COLUMNS;
       if (g.tile != 32) fmt = WPROJ_INDEX_COLUMNS;
       p->fmt = fmt;
       if (fmt == WPROJ_INDEX_TILE_MASK) {
@@ -871,13 +882,15 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
           k_sel_hist<2><<<hgrid, 256, 0, s>>>(bb.K, S, bsel.as<SelState>(), hcnt.as<unsigned>(), hq.as<unsigned long long>());
           k_sel_find<2><<<nb, 256, 0, s>>>(bsel.as<SelState>(), hcnt.as<unsigned>(), hq.as<unsigned long long>(), e_target);
           WPROJ_CHECK_LAUNCH("select");
-          const int nt_max = (g.G / g.tile) * (g.G / g.tile);
-          const size_t smem = (nt_max <= 4096) ? sizeof(int32_t) * 2 * nt_max : 0;
+          const int nt_box = box_tiles(S, g);
+          const int smem_tiles = std::min(nt_box, 4096);
+          const size_t smem = sizeof(int32_t) * 2 * smem_tiles;
           if (smem > 48 * 1024) {
             WPROJ_CUDA(cudaFuncSetAttribute(k_tile_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
           }
           k_tile_count<<<hgrid, 256, smem, s>>>(bb.K, S, ids, d_j0.as<int2>(), d_segbase.as<int64_t>(), g,
-                                                bsel.as<SelState>(), d_cntgt.as<int32_t>(), d_cnteq.as<int32_t>());
+                                                bsel.as<SelState>(), d_cntgt.as<int32_t>(), d_cnteq.as<int32_t>(),
+                                                smem_tiles);
           WPROJ_CHECK_LAUNCH("tile count");
           k_tie_alloc<<<ceil_div(nb, 128), 128, 0, s>>>(nb, ids, d_segbase.as<int64_t>(), d_ntile.as<int32_t>(),
                                                        bsel.as<SelState>(), d_cntgt.as<int32_t>(),
@@ -886,8 +899,7 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
                                                        r_ntie.as<int32_t>(), r_all.as<int8_t>(), r_max.as<float>());
           WPROJ_CHECK_LAUNCH("tie alloc");
         } else {
-          const int nt_max = (g.G / g.tile) * (g.G / g.tile);
-          const int gx = std::min(nt_max, 1024);
+          const int gx = std::min(box_tiles(S, g), 1024);   // the kernel strides over more
           k_emit<<<dim3(gx, nb), 256, 0, s>>>(bb.K, S, ids, d_j0.as<int2>(), d_segbase.as<int64_t>(),
                                               d_ntile.as<int32_t>(), g, p->seg_off.as<int64_t>(),
                                               d_tieb.as<int32_t>(), r_thr.as<uint32_t>(), r_ntie.as<int32_t>(),

@@ -55,6 +55,8 @@ class Workload:
     inner_iters: int = 10
     snr_in_db: float = 30.0
     powerlaw: bool = False
+    w_unit: str = "wd"       # "wd": w = w_d N / L^2;  "cells": chirp half-band h = 2 w_c cells, w = h / L^2
+    box: str = "G"           # kernel box: "G" (exact) or "rule" (S(w))
     extra: dict = field(default_factory=dict)
 
 
@@ -65,6 +67,10 @@ SMALL = Workload("blobs64_m1229", N=64, n_blobs=20, M=1229, uv="uniform",
 PAPER_SCALE = Workload("blobs256_m32768", N=256, n_blobs=200, M=32768,
                        uv="gaussian", sigma_uv=0.25, wd_max=1.0, e=0.99,
                        dr_iters=300)
+# The precision-form case: 1024x1024, 2000 blobs plus a power-law diffuse part,
+# M = 2^21, w_c ~ U[0, 4] grid cells (chirp half-band h = 2 w_c), box rule S(w).
+PRECISION = Workload("blobs1024_m2097152", N=1024, n_blobs=2000, M=2 ** 21, uv="uniform",
+                     wd_max=4.0, e=0.99, dr_iters=50, powerlaw=True, w_unit="cells", box="rule")
 
 
 def blob_sky(rng: np.random.Generator, N: int, n_blobs: int) -> np.ndarray:
@@ -74,12 +80,15 @@ def blob_sky(rng: np.random.Generator, N: int, n_blobs: int) -> np.ndarray:
     cy = rng.uniform(0.0, N, n_blobs)
     amp = rng.uniform(0.0, 1.0, n_blobs)
     sig = rng.uniform(1.0, 4.0, n_blobs)
-    p = np.arange(N, dtype=np.float64)
     x = np.zeros((N, N), dtype=np.float64)
     for b in range(n_blobs):
-        gx = np.exp(-((p - cx[b]) ** 2) / (2.0 * sig[b] ** 2))
-        gy = np.exp(-((p - cy[b]) ** 2) / (2.0 * sig[b] ** 2))
-        x += amp[b] * np.outer(gx, gy)
+        # each blob within +-8 sigma of its centre (the rest is below 1e-13 of its peak)
+        r = int(np.ceil(8.0 * sig[b]))
+        pu = np.arange(max(0, int(cx[b]) - r), min(N, int(cx[b]) + r + 2), dtype=np.float64)
+        pv = np.arange(max(0, int(cy[b]) - r), min(N, int(cy[b]) + r + 2), dtype=np.float64)
+        gx = np.exp(-((pu - cx[b]) ** 2) / (2.0 * sig[b] ** 2))
+        gy = np.exp(-((pv - cy[b]) ** 2) / (2.0 * sig[b] ** 2))
+        x[int(pu[0]):int(pu[-1]) + 1, int(pv[0]):int(pv[-1]) + 1] += amp[b] * np.outer(gx, gy)
     return x
 
 
@@ -152,7 +161,10 @@ def make_problem(wl: Workload, seed: int = 0, M: int | None = None,
         wd = rng.uniform(0.0, wl.wd_max, M)
     else:
         wd = np.full(M, float(wd_const))
-    w = w_from_wd(wd, N, L)
+    if wl.w_unit == "cells":
+        w = 2.0 * wd / (L * L)          # h = 2 w_c cells; h = |w| L^2
+    else:
+        w = w_from_wd(wd, N, L)
     uvw = np.ascontiguousarray(np.concatenate([uv, w[:, None]], axis=1))
     return Problem(wl, L, x, uvw, wd, rng)
 
