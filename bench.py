@@ -280,7 +280,7 @@ def run_ours(args):
     build_s = time.perf_counter() - t0
     st = plan.stats()
     csrv = plan.csr()
-    fmt, n_seg = csrv.index_format, csrv.n_seg
+    fmt, n_seg, stream_bytes = csrv.index_format, csrv.n_seg, csrv.stream_bytes
     del csrv
     nnz, M, G = st["nnz"], st["m"], plan.G
 
@@ -353,10 +353,10 @@ def run_ours(args):
     grid_ms = kst["t_grid_ms"] / max(1, kst["n_grid"])
     alg_deg = nnz * b_val + M * 8 + G * G * 8
     alg_grid = nnz * b_val + M * 8 + G * G * 8
-    idx_bytes = nnz * 4 if fmt == "columns" else n_seg * 128
-    stored = nnz * b_val + idx_bytes
-    # kernel labels as in profiles/: k_tiles<VDT, degrid?> for the tile-mask format
-    deg_name, grid_name = ("k_tiles_degrid", "k_tiles_grid") if fmt == "mask" else ("k_degrid", "k_grid")
+    # G as stored: values + column indices, or the tile-stream records
+    stored = nnz * (b_val + 4) if fmt == "columns" else stream_bytes
+    # kernel labels as in profiles/: k_stream<VDT, degrid?> for the tile stream
+    deg_name, grid_name = ("k_stream_degrid", "k_stream_grid") if fmt == "mask" else ("k_degrid", "k_grid")
     if kst["t_degrid_ms"] >= kst["t_grid_ms"]:
         dom, ms, alg, kname = "degrid", deg_ms, alg_deg, deg_name
     else:
@@ -383,7 +383,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(wl, e, {"nnz": nnz, "G_bytes": stored, "index_format": fmt,
+            "config": workload_config(wl, e, {"nnz": nnz, "segments": n_seg, "G_bytes": stored, "index_format": fmt,
                                               "value_dtype": args.value_dtype,
                                               "l2": "inputs larger than L2 (G exceeds L2 many times)",
                                               "parallelism": f"replicas x{ws}"}),

@@ -80,12 +80,20 @@ typedef struct {
   int32_t index_format; /* wproj_index_format: how the columns of G are stored */
 } wproj_grid_desc;
 
-/* Column storage of G.  Entries of a row are grouped by 32 x 32 grid tile (tiles
- * ascending) and stored row-major inside a tile, so each (row, tile) segment can
- * carry its columns either as int32 indices (4 B per entry) or as a 32-word bit
- * mask of the tile (bit l of word r = cell (r, l) is stored; 128 B per segment).
- * AUTO picks the mask when segments average >= 256 entries (dense rows), the
- * indices otherwise. */
+/* Storage of G.  The entries of a row are grouped by 32 x 32 grid tile (tiles
+ * ascending) and ordered row-major inside a tile; a (row, tile) pair with
+ * entries is a segment.  Two formats:
+ *   COLUMNS      CSR: row_ptr, int32 column indices (4 B per entry) and values,
+ *                row after row;
+ *   TILE_MASK    a tile stream: for every tile (ascending) and every row with
+ *                entries in it (rows ascending), one record, 16-byte aligned:
+ *                  int32 row, int32 count, int32 segment id, int32 0   (16 B)
+ *                  32 uint32 mask words, bit l of word r = cell (r, l) stored
+ *                  count values in row-major cell order, zero-padded to 16 B
+ *                (128 B of mask per segment instead of 4 B per entry, and each
+ *                tile's records contiguous for streaming).
+ * AUTO picks TILE_MASK when segments average >= 256 entries (dense rows), COLUMNS
+ * otherwise.  wproj_csr_rows exports any rows in CSR order from either format. */
 typedef enum { WPROJ_INDEX_AUTO = 0, WPROJ_INDEX_COLUMNS = 1, WPROJ_INDEX_TILE_MASK = 2 } wproj_index_format;
 
 /* View of G held by a plan (device pointers owned by the plan; valid until the
@@ -94,20 +102,26 @@ typedef struct {
   int64_t m;                /* rows (visibilities) */
   int64_t nnz;              /* stored entries */
   int64_t n_cols;           /* G * G */
-  const int64_t *row_ptr;   /* m + 1 offsets */
-  const int32_t *col;       /* nnz column indices (WPROJ_INDEX_COLUMNS), else NULL: use
-                               wproj_csr_columns to expand the tile masks */
-  const void *val;          /* nnz complex values: float2, or (bf16, bf16) / (f16, f16) pairs */
-  const float *row_scale;   /* m scales (bf16/f16), NULL for f32 */
+  const int64_t *row_ptr;   /* m + 1 offsets of each row's entries in CSR order (both formats) */
+  const int32_t *col;       /* COLUMNS: nnz column indices; TILE_MASK: NULL */
+  const void *val;          /* COLUMNS: nnz complex values in CSR order, float2 or (bf16, bf16) /
+                               (f16, f16) pairs; TILE_MASK: NULL */
+  const float *row_scale;   /* m scales (bf16/f16: G[k, q] = row_scale[k] * stored value),
+                               NULL for f32 */
   int32_t value_dtype;
   int32_t index_format;     /* WPROJ_INDEX_COLUMNS or WPROJ_INDEX_TILE_MASK */
   int64_t n_seg;            /* (row, tile) segments */
-  const uint32_t *tile_mask;  /* n_seg x 32 words (tile-mask format), else NULL */
+  const void *stream;       /* TILE_MASK: the record stream; else NULL */
+  int64_t stream_bytes;     /* its size in bytes (0 for COLUMNS) */
 } wproj_csr;
 
-/* Column index of every stored entry of G (nnz int32, CSR order) written to
- * col_out (device), whatever the index format. */
-wproj_status wproj_csr_columns(const wproj_plan *p, int32_t *col_out, void *stream);
+/* Entries of rows [k0, k1) of G in CSR order, whatever the index format:
+ * col_out (int32, device) receives their column indices and val_out (device)
+ * their stored values (the plan's value dtype, unscaled), each
+ * row_ptr[k1] - row_ptr[k0] long; either may be NULL.  Synchronises `stream`
+ * once (to read the range).  0 <= k0 <= k1 <= m, else WPROJ_ERR_INVALID_ARG. */
+wproj_status wproj_csr_rows(const wproj_plan *p, int64_t k0, int64_t k1, int32_t *col_out, void *val_out,
+                            void *stream);
 
 /* Douglas-Rachford parameters (the paper states none; these are the defaults
  * used by the oracle and the benchmarks). */
@@ -143,9 +157,6 @@ typedef struct {
   double t_fft_ms, t_degrid_ms, t_grid_ms, t_reduce_ms, t_solver_ms;
   int64_t n_fft, n_degrid, n_grid, n_reduce, n_solver;
   int64_t launches;          /* kernels launched by Phi, Phi^H and the solver since the last reset */
-  int32_t device_errors;     /* error bits raised on the device since the plan was created:
-                                1 = a staged copy of G did not arrive within ~1 s (the block
-                                gave up; results of that call are invalid) */
 } wproj_stats;
 
 /* ---- plan ---------------------------------------------------------------- */

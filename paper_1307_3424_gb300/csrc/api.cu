@@ -178,9 +178,6 @@ wproj_status wproj_plan_create(wproj_plan **out, const wproj_grid_desc *d) {
   chk(p->Xt2.alloc(sizeof(float2) * size_t(G) * G));
   chk(p->inter.alloc(sizeof(float2) * size_t(g.N) * G));
   chk(p->xtmp.alloc(sizeof(float) * size_t(g.N) * g.N));
-  chk(p->dev_err.alloc(sizeof(int)));
-  if (st == WPROJ_OK && cudaMemset(p->dev_err.ptr, 0, sizeof(int)) != cudaSuccess)
-    st = fail(WPROJ_ERR_CUDA, "plan init: memset");
   if (st == WPROJ_OK) {
     k_inv_a<<<ceil_div(g.N, 256), 256, 0, s>>>(g.N, g.W, g.beta, p->inv_a.as<float>());
     cudaError_t err = cudaGetLastError();
@@ -224,22 +221,23 @@ wproj_status wproj_get_csr(const wproj_plan *p, wproj_csr *out) {
   out->nnz = p->nnz;
   out->n_cols = int64_t(p->g.G) * p->g.G;
   out->row_ptr = p->row_ptr.as<int64_t>();
-  out->col = p->col.as<int32_t>();
-  out->val = p->val.ptr;
   out->row_scale = p->g.value_dtype == WPROJ_VAL_F32 ? nullptr : p->row_scale.as<float>();
   out->value_dtype = p->g.value_dtype;
   out->index_format = p->fmt;
   out->n_seg = p->n_seg;
-  out->col = p->fmt == WPROJ_INDEX_COLUMNS ? p->col.as<int32_t>() : nullptr;
-  out->tile_mask = p->fmt == WPROJ_INDEX_TILE_MASK ? p->seg_mask.as<uint32_t>() : nullptr;
+  const bool cols = p->fmt == WPROJ_INDEX_COLUMNS;
+  out->col = cols ? p->col.as<int32_t>() : nullptr;
+  out->val = cols ? p->val.ptr : nullptr;
+  out->stream = cols ? nullptr : p->stream.ptr;
+  out->stream_bytes = cols ? 0 : p->stream_bytes;
   return WPROJ_OK;
 }
 
-wproj_status wproj_csr_columns(const wproj_plan *p, int32_t *col_out, void *stream) {
+wproj_status wproj_csr_rows(const wproj_plan *p, int64_t k0, int64_t k1, int32_t *col_out, void *val_out,
+                            void *stream) {
   WPROJ_TRY(check_built(p));
-  if (!col_out) return fail(WPROJ_ERR_INVALID_ARG, "null col_out");
-  return csr_columns(p, col_out, as_stream(stream));
-  return WPROJ_OK;
+  if (k0 < 0 || k1 < k0 || k1 > p->m) return fail(WPROJ_ERR_INVALID_ARG, "csr_rows: need 0 <= k0 <= k1 <= m");
+  return csr_rows(p, k0, k1, col_out, val_out, as_stream(stream));
 }
 
 wproj_status wproj_phi(wproj_plan *p, const float *x, void *y, void *stream) {
@@ -350,9 +348,6 @@ wproj_status wproj_get_stats(wproj_plan *p, wproj_stats *out) {
   out->n_reduce = p->timer.count[TC_REDUCE];
   out->n_solver = p->timer.count[TC_SOLVER];
   out->launches = p->launches;
-  int e = 0;
-  WPROJ_CUDA(cudaMemcpy(&e, p->dev_err.ptr, sizeof(int), cudaMemcpyDeviceToHost));
-  out->device_errors = e;
   return WPROJ_OK;
 }
 

@@ -41,11 +41,6 @@ constexpr int kSelChunk = 8192;          // entries per histogram block
 // fill the GPU and large ones keep the partial sums small.
 int64_t degrid_piece(int64_t nnz) { return std::min<int64_t>(16384, std::max<int64_t>(512, nnz / (152 * 64))); }
 int64_t grid_chunk(int64_t nnz) { return std::min<int64_t>(262144, std::max<int64_t>(4096, nnz / (152 * 16))); }
-// segments per degridding piece in the tile-mask format (about degrid_piece entries)
-int64_t seg_piece(int64_t nnz, int64_t n_seg) {
-  const int64_t avg = std::max<int64_t>(1, nnz / std::max<int64_t>(1, n_seg));
-  return std::min<int64_t>(4096, std::max<int64_t>(1, degrid_piece(nnz) / avg));
-}
 
 enum : int { ERR_NONFINITE = 1, ERR_BAND = 2, ERR_EMIT = 4 };
 
@@ -502,8 +497,8 @@ k_emit(const float2 *__restrict__ K, int S, const int32_t *__restrict__ ids,
        const int32_t *__restrict__ seg_tieb, const uint32_t *__restrict__ r_thr,
        const int32_t *__restrict__ r_ntie, const int8_t *__restrict__ r_all,
        const float *__restrict__ r_max, const int32_t *__restrict__ seg_cnt,
-       int32_t *__restrict__ col, uint32_t *__restrict__ mask, int fmt, void *__restrict__ val, int vdt,
-       int *__restrict__ err) {
+       int32_t *__restrict__ col, int fmt, void *__restrict__ val, int vdt,
+       const int64_t *__restrict__ seg_rec, unsigned char *__restrict__ stream, int *__restrict__ err) {
   __shared__ unsigned tiew[32], selw[32];
   __shared__ int tiepre[32], selpre[33];
   const int b = blockIdx.y;
@@ -576,33 +571,40 @@ k_emit(const float2 *__restrict__ K, int S, const int32_t *__restrict__ ids,
       if (lane == 31) selpre[32] = inc;
     }
     __syncthreads();
-    const int64_t o = seg_off[sid];
     const int cnt = seg_cnt[sid];
     if (threadIdx.x == 0 && selpre[32] != cnt) atomicOr(err, ERR_EMIT);
+    // COLUMNS: entries at seg_off in col / val; TILE_MASK: the segment's record
+    const bool rec = fmt == WPROJ_INDEX_TILE_MASK;
+    const int64_t o = rec ? 0 : seg_off[sid];
+    unsigned char *rp = rec ? stream + seg_rec[sid] : nullptr;
+    void *vdst = rec ? static_cast<void *>(rp + kRecValues) : val;
     for (int rr = 0; rr < 4; ++rr) {
       if (!sel[rr]) continue;
       const int r = 4 * w + rr;
       const int pos = selpre[r] + __popc(selw[r] & lt);
       if (pos >= cnt) continue;      // never taken when the two passes agree
       const int64_t at = o + pos;
-      if (fmt == WPROJ_INDEX_COLUMNS) col[at] = (tile_u * TS + r) * g.G + tile_v * TS + lane;
+      if (!rec) col[at] = (tile_u * TS + r) * g.G + tile_v * TS + lane;
       const float2 v = Kb[kidx[rr]];
       if (vdt == WPROJ_VAL_F32) {
-        reinterpret_cast<float2 *>(val)[at] = v;
+        reinterpret_cast<float2 *>(vdst)[at] = v;
       } else if (vdt == WPROJ_VAL_BF16) {
-        reinterpret_cast<__nv_bfloat162 *>(val)[at] = __floats2bfloat162_rn(v.x * inv_scale, v.y * inv_scale);
+        reinterpret_cast<__nv_bfloat162 *>(vdst)[at] = __floats2bfloat162_rn(v.x * inv_scale, v.y * inv_scale);
       } else {
-        reinterpret_cast<__half2 *>(val)[at] = __floats2half2_rn(v.x * inv_scale, v.y * inv_scale);
+        reinterpret_cast<__half2 *>(vdst)[at] = __floats2half2_rn(v.x * inv_scale, v.y * inv_scale);
       }
     }
-    if (fmt == WPROJ_INDEX_TILE_MASK && w == 0) mask[sid * 32 + lane] = selw[lane];
+    if (rec) {
+      if (w == 0) reinterpret_cast<uint32_t *>(rp + kRecHeader)[lane] = selw[lane];
+      if (threadIdx.x == 0) *reinterpret_cast<int4 *>(rp) = make_int4(k, cnt, int(sid), 0);
+    }
     __syncthreads();
   }
 }
 
 __global__ void k_row_ptr(int64_t m, const int64_t *__restrict__ seg_base,
                           const int64_t *__restrict__ seg_off, const int32_t *__restrict__ ntile,
-                          int64_t n_seg, int64_t nnz, int64_t piece, int fmt, int64_t seg_piece,
+                          int64_t n_seg, int64_t nnz, int64_t piece, int fmt,
                           int64_t *__restrict__ row_ptr, int32_t *__restrict__ npieces) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k > m) return;
@@ -611,33 +613,22 @@ __global__ void k_row_ptr(int64_t m, const int64_t *__restrict__ seg_base,
   const int64_t start = (sb < n_seg) ? seg_off[sb] : nnz;
   const int64_t end = (k + 1 < m) ? ((seg_base[k + 1] < n_seg) ? seg_off[seg_base[k + 1]] : nnz) : nnz;
   row_ptr[k] = start;
-  if (fmt == WPROJ_INDEX_TILE_MASK) {
-    npieces[k] = int32_t(i64max(1, (ntile[k] + seg_piece - 1) / seg_piece));
-  } else {
-    const int64_t n = end - start;
-    npieces[k] = int32_t(i64max(1, (n + piece - 1) / piece));
-  }
+  (void)ntile;
+  // row pieces of the column-format degridding (the tile stream has none)
+  npieces[k] = fmt == WPROJ_INDEX_TILE_MASK ? 0 : int32_t(i64max(1, (end - start + piece - 1) / piece));
 }
 
-// Row pieces of the degridding: ranges of entries (column format) or of
-// segments (tile-mask format).
+// Row pieces of the column-format degridding: ranges of <= piece entries.
 __global__ void k_pieces(int64_t m, const int64_t *__restrict__ row_ptr,
                          const int64_t *__restrict__ piece_base, int32_t *__restrict__ piece_row,
                          int64_t *__restrict__ piece_lo, int32_t *__restrict__ piece_len,
-                         int32_t *__restrict__ row_piece_ptr, int64_t n_pieces, int64_t piece, int fmt,
-                         int64_t seg_piece, const int64_t *__restrict__ seg_base,
-                         const int32_t *__restrict__ ntile) {
+                         int32_t *__restrict__ row_piece_ptr, int64_t n_pieces, int64_t piece) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k > m) return;
   if (k == m) { row_piece_ptr[m] = int32_t(n_pieces); return; }
   const int64_t pb = piece_base[k];
   row_piece_ptr[k] = int32_t(pb);
-  int64_t lo, n, step;
-  if (fmt == WPROJ_INDEX_TILE_MASK) {
-    lo = seg_base[k]; n = ntile[k]; step = seg_piece;
-  } else {
-    lo = row_ptr[k]; n = row_ptr[k + 1] - lo; step = piece;
-  }
+  const int64_t lo = row_ptr[k], n = row_ptr[k + 1] - lo, step = piece;
   const int np = int(i64max(1, (n + step - 1) / step));
   for (int i = 0; i < np; ++i) {
     piece_row[pb + i] = int32_t(k);
@@ -650,19 +641,35 @@ __global__ void k_pieces(int64_t m, const int64_t *__restrict__ row_ptr,
 __global__ void k_gather_cnt(int64_t n, const int32_t *__restrict__ tile_seg,
                              const int32_t *__restrict__ seg_cnt, const int64_t *__restrict__ seg_off,
                              const int32_t *__restrict__ seg_row, int32_t *__restrict__ out,
-                             SegMeta *__restrict__ meta, int fmt) {
+                             SegMeta *__restrict__ meta) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int sg = tile_seg[i];
   const int c = seg_cnt[sg];
   out[i] = c;
+  if (!meta) return;
   SegMeta m;
   m.off_cnt = (unsigned long long)seg_off[sg] | ((unsigned long long)c << 40);
   m.seg = sg;
-  (void)fmt;
   m.row = seg_row[sg];
   meta[i] = m;
 }
+
+// tile-stream layout: record bytes of each segment in tile order
+__global__ void k_rec_size(int64_t n, const int32_t *__restrict__ tile_seg, const int32_t *__restrict__ seg_cnt,
+                           int vb, int32_t *__restrict__ out) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  out[i] = kRecValues + ((seg_cnt[tile_seg[i]] * vb + 15) & ~15);
+}
+
+__global__ void k_rec_scatter(int64_t n, const int32_t *__restrict__ tile_seg, const int64_t *__restrict__ rec_off,
+                              int64_t *__restrict__ seg_rec) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  seg_rec[tile_seg[i]] = rec_off[i];
+}
+
 
 __global__ void k_tile_chunks(int n_tiles, const int64_t *__restrict__ tile_ptr,
                               const int64_t *__restrict__ cum, int64_t n_seg, int64_t nnz_total,
@@ -804,7 +811,9 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
 
   const double e_target = e + kSelectMargin;
   const int vdt = g.value_dtype;
-  DevBuf d_pieces_n;
+  const int vb = vdt == WPROJ_VAL_F32 ? 8 : 4;
+  const int n_tiles = g.nT * g.nT;
+  DevBuf d_pieces_n, tile_seg, tptr;
 
   for (int phase = 1; phase <= 2; ++phase) {
     if (phase == 2) {
@@ -826,21 +835,52 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
       if (fmt == WPROJ_INDEX_AUTO) fmt = (p->nnz >= 256 * n_seg) ? WPROJ_INDEX_TILE_MASK : WPROJ_INDEX_COLUMNS;
       if (g.tile != 32) fmt = WPROJ_INDEX_COLUMNS;
       p->fmt = fmt;
+      // segments in tile order, rows ascending inside a tile: the gridding's
+      // order, and the record order of the tile stream
+      WPROJ_TRY(tile_seg.alloc(sizeof(int32_t) * std::max<int64_t>(1, n_seg)));
+      WPROJ_TRY(tptr.alloc(sizeof(int64_t) * (n_tiles + 1)));
+      WPROJ_TRY(stable_bin_sort(p->seg_tile.as<int32_t>(), n_seg, n_tiles, tile_seg.as<int32_t>(),
+                                tptr.as<int64_t>(), s));
       if (fmt == WPROJ_INDEX_TILE_MASK) {
         p->col.release();
-        WPROJ_TRY(p->seg_mask.alloc(sizeof(uint32_t) * 32 * std::max<int64_t>(1, n_seg)));
+        p->val.release();
+        p->seg_meta.release();
+        DevBuf rsz;
+        WPROJ_TRY(rsz.alloc(sizeof(int32_t) * std::max<int64_t>(1, n_seg)));
+        WPROJ_TRY(p->rec_off.alloc(sizeof(int64_t) * (n_seg + 1)));
+        WPROJ_TRY(p->seg_rec.alloc(sizeof(int64_t) * std::max<int64_t>(1, n_seg)));
+        int64_t total = 0;
+        if (n_seg > 0) {
+          k_rec_size<<<ceil_div(n_seg, 256), 256, 0, s>>>(n_seg, tile_seg.as<int32_t>(), p->seg_cnt.as<int32_t>(), vb,
+                                                          rsz.as<int32_t>());
+          WPROJ_CHECK_LAUNCH("record sizes");
+          WPROJ_TRY(exclusive_scan_i32_to_i64(rsz.as<int32_t>(), p->rec_off.as<int64_t>(), n_seg, s));
+          int64_t lo2 = 0;
+          int32_t lc2 = 0;
+          WPROJ_CUDA(cudaMemcpy(&lo2, p->rec_off.as<int64_t>() + (n_seg - 1), sizeof(int64_t), cudaMemcpyDeviceToHost));
+          WPROJ_CUDA(cudaMemcpy(&lc2, rsz.as<int32_t>() + (n_seg - 1), sizeof(int32_t), cudaMemcpyDeviceToHost));
+          total = lo2 + lc2;
+          k_rec_scatter<<<ceil_div(n_seg, 256), 256, 0, s>>>(n_seg, tile_seg.as<int32_t>(), p->rec_off.as<int64_t>(),
+                                                             p->seg_rec.as<int64_t>());
+          WPROJ_CHECK_LAUNCH("record offsets");
+        }
+        WPROJ_CUDA(cudaMemcpy(p->rec_off.as<int64_t>() + n_seg, &total, sizeof(int64_t), cudaMemcpyHostToDevice));
+        WPROJ_TRY(p->stream.alloc(std::max<int64_t>(16, total)));
+        WPROJ_CUDA(cudaMemsetAsync(p->stream.ptr, 0, std::max<int64_t>(16, total), s));   // record padding
+        p->stream_bytes = total;
       } else {
-        p->seg_mask.release();
+        p->stream.release();
+        p->seg_rec.release();
+        p->rec_off.release();
+        p->stream_bytes = 0;
         WPROJ_TRY(p->col.alloc(sizeof(int32_t) * std::max<int64_t>(1, p->nnz)));
+        WPROJ_TRY(p->val.alloc(int64_t(vb) * std::max<int64_t>(1, p->nnz)));
       }
-      // 16 bytes of slack: staged copies widen each value run to 16-byte bounds
-      WPROJ_TRY(p->val.alloc((vdt == WPROJ_VAL_F32 ? 8 : 4) * std::max<int64_t>(1, p->nnz) + 16));
       WPROJ_TRY(p->row_ptr.alloc(sizeof(int64_t) * (m + 1)));
       WPROJ_TRY(d_pieces_n.alloc(sizeof(int32_t) * (m + 1)));
       k_row_ptr<<<ceil_div(m + 1, 256), 256, 0, s>>>(m, d_segbase.as<int64_t>(), p->seg_off.as<int64_t>(),
                                                      d_ntile.as<int32_t>(), n_seg, p->nnz, degrid_piece(p->nnz),
-                                                     p->fmt, seg_piece(p->nnz, n_seg), p->row_ptr.as<int64_t>(),
-                                                     d_pieces_n.as<int32_t>());
+                                                     p->fmt, p->row_ptr.as<int64_t>(), d_pieces_n.as<int32_t>());
       WPROJ_CHECK_LAUNCH("row ptr");
     }
     for (int c = 0; c < 9; ++c) {
@@ -904,8 +944,9 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
                                               d_ntile.as<int32_t>(), g, p->seg_off.as<int64_t>(),
                                               d_tieb.as<int32_t>(), r_thr.as<uint32_t>(), r_ntie.as<int32_t>(),
                                               r_all.as<int8_t>(), r_max.as<float>(), p->seg_cnt.as<int32_t>(),
-                                              p->col.as<int32_t>(), p->seg_mask.as<uint32_t>(), p->fmt,
-                                              p->val.ptr, vdt, d_err.as<int>());
+                                              p->col.as<int32_t>(), p->fmt, p->val.ptr, vdt,
+                                              p->seg_rec.as<int64_t>(), p->stream.as<unsigned char>(),
+                                              d_err.as<int>());
           WPROJ_CHECK_LAUNCH("emit");
         }
       }
@@ -919,8 +960,15 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
     p->row_scale.release();
   }
 
-  // ---- degridding pieces
-  {
+  // ---- degridding: row pieces (COLUMNS) or one partial per (segment, warp) (TILE_MASK)
+  if (p->fmt == WPROJ_INDEX_TILE_MASK) {
+    p->n_pieces = 0;
+    p->piece_row.release();
+    p->piece_lo.release();
+    p->piece_len.release();
+    p->row_piece_ptr.release();
+    WPROJ_TRY(p->piece_partial.alloc(sizeof(float2) * std::max<int64_t>(1, kStreamWarps * n_seg)));
+  } else {
     DevBuf pbase;
     WPROJ_TRY(pbase.alloc(sizeof(int64_t) * (m + 1)));
     WPROJ_TRY(exclusive_scan_i32_to_i64(d_pieces_n.as<int32_t>(), pbase.as<int64_t>(), m, s));
@@ -933,39 +981,34 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
     WPROJ_TRY(p->piece_lo.alloc(sizeof(int64_t) * p->n_pieces));
     WPROJ_TRY(p->piece_len.alloc(sizeof(int32_t) * p->n_pieces));
     WPROJ_TRY(p->row_piece_ptr.alloc(sizeof(int32_t) * (m + 1)));
-    WPROJ_TRY(p->piece_partial.alloc(sizeof(float2) *
-                                     std::max<int64_t>(1, p->fmt == WPROJ_INDEX_TILE_MASK ? 4 * n_seg : p->n_pieces)));
+    WPROJ_TRY(p->piece_partial.alloc(sizeof(float2) * std::max<int64_t>(1, p->n_pieces)));
     k_pieces<<<ceil_div(m + 1, 256), 256, 0, s>>>(m, p->row_ptr.as<int64_t>(), pbase.as<int64_t>(),
                                                   p->piece_row.as<int32_t>(), p->piece_lo.as<int64_t>(),
                                                   p->piece_len.as<int32_t>(), p->row_piece_ptr.as<int32_t>(),
-                                                  p->n_pieces, degrid_piece(p->nnz), p->fmt,
-                                                  seg_piece(p->nnz, n_seg), d_segbase.as<int64_t>(),
-                                                  d_ntile.as<int32_t>());
+                                                  p->n_pieces, degrid_piece(p->nnz));
     WPROJ_CHECK_LAUNCH("pieces");
   }
 
-  // ---- gridding: segments by tile (rows ascending), chunks of ~kGridChunk entries
+  // ---- gridding: chunks of one tile's segments (tile order), balanced by entries
   {
-    const int n_tiles = g.nT * g.nT;
-    DevBuf tptr, cntsorted, cum, nch, chbase;
-    WPROJ_TRY(p->tile_seg.alloc(sizeof(int32_t) * std::max<int64_t>(1, n_seg)));
-    WPROJ_TRY(tptr.alloc(sizeof(int64_t) * (n_tiles + 1)));
-    WPROJ_TRY(stable_bin_sort(p->seg_tile.as<int32_t>(), n_seg, n_tiles, p->tile_seg.as<int32_t>(),
-                              tptr.as<int64_t>(), s));
+    const bool rec = p->fmt == WPROJ_INDEX_TILE_MASK;
+    const int64_t chunk = grid_chunk(p->nnz);
+    DevBuf cntsorted, cum, nch, chbase;
     WPROJ_TRY(cntsorted.alloc(sizeof(int32_t) * std::max<int64_t>(1, n_seg)));
     WPROJ_TRY(cum.alloc(sizeof(int64_t) * std::max<int64_t>(1, n_seg)));
-    WPROJ_TRY(p->seg_meta.alloc(sizeof(SegMeta) * std::max<int64_t>(1, n_seg)));
+    if (!rec) WPROJ_TRY(p->seg_meta.alloc(sizeof(SegMeta) * std::max<int64_t>(1, n_seg)));
     if (n_seg > 0) {
-      k_gather_cnt<<<ceil_div(n_seg, 256), 256, 0, s>>>(n_seg, p->tile_seg.as<int32_t>(), p->seg_cnt.as<int32_t>(),
+      k_gather_cnt<<<ceil_div(n_seg, 256), 256, 0, s>>>(n_seg, tile_seg.as<int32_t>(), p->seg_cnt.as<int32_t>(),
                                                         p->seg_off.as<int64_t>(), p->seg_row.as<int32_t>(),
-                                                        cntsorted.as<int32_t>(), p->seg_meta.as<SegMeta>(), p->fmt);
+                                                        cntsorted.as<int32_t>(),
+                                                        rec ? nullptr : p->seg_meta.as<SegMeta>());
       WPROJ_CHECK_LAUNCH("gather cnt");
       WPROJ_TRY(exclusive_scan_i32_to_i64(cntsorted.as<int32_t>(), cum.as<int64_t>(), n_seg, s));
     }
     WPROJ_TRY(nch.alloc(sizeof(int32_t) * n_tiles));
     WPROJ_TRY(chbase.alloc(sizeof(int64_t) * (n_tiles + 1)));
     k_tile_chunks<<<ceil_div(n_tiles, 256), 256, 0, s>>>(n_tiles, tptr.as<int64_t>(), cum.as<int64_t>(), n_seg,
-                                                         p->nnz, grid_chunk(p->nnz), nch.as<int32_t>());
+                                                         p->nnz, chunk, nch.as<int32_t>());
     WPROJ_CHECK_LAUNCH("tile chunks");
     WPROJ_TRY(exclusive_scan_i32_to_i64(nch.as<int32_t>(), chbase.as<int64_t>(), n_tiles, s));
     int64_t lb = 0;
@@ -980,8 +1023,7 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
     k_chunk_fill<<<ceil_div(n_tiles + 1, 256), 256, 0, s>>>(n_tiles, tptr.as<int64_t>(), cum.as<int64_t>(), n_seg,
                                                             p->nnz, chbase.as<int64_t>(), p->chunk_tile.as<int32_t>(),
                                                             p->chunk_lo.as<int64_t>(), p->chunk_hi.as<int64_t>(),
-                                                            p->tile_chunk_ptr.as<int32_t>(), p->n_chunks,
-                                                            grid_chunk(p->nnz));
+                                                            p->tile_chunk_ptr.as<int32_t>(), p->n_chunks, chunk);
     WPROJ_CHECK_LAUNCH("chunk fill");
     WPROJ_TRY(p->grid_partial.alloc(sizeof(float2) * size_t(p->n_chunks) * g.tile * g.tile));
   }

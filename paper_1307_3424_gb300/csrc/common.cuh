@@ -14,6 +14,13 @@ namespace wproj {
 
 constexpr int kTile = 32;          // side of the grid tiles used for gridding and CSR order
 constexpr double kSelectMargin = 1e-5;   // extra kept energy fraction (covers FP32 error)
+// tile-stream records (TILE_MASK format): 16-byte header (row, count, segment
+// id, 0), 32 mask words, then the values from this byte offset on
+constexpr int kRecHeader = 16;
+constexpr int kRecValues = kRecHeader + 32 * 4;
+// consumer warps of the tile-stream kernels: the degridding leaves one partial
+// sum per (record, warp)
+constexpr int kStreamWarps = 4;
 
 // ---- complex helpers --------------------------------------------------------
 __host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {

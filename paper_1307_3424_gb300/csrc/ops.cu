@@ -1,4 +1,5 @@
 // Part II: the measurement operator Phi = G F Z A (Eq. 8) and its adjoint.
+// Kernels for G in the COLUMNS format (TILE_MASK: tiles.cu) and the dispatch:
 //
 //  degridding  y_k = sum_q G[k, q] X[q]          warp per row piece (<= 16384
 //              entries), partial sums reduced per row in a fixed order
@@ -164,44 +165,6 @@ __global__ void k_grid_reduce(const int32_t *__restrict__ tile_chunk_ptr, const 
 
 constexpr int kGridWarps = 8;
 
-// ---- tile-mask format -----------------------------------------------------------------
-// A segment is a (row, 32x32 tile) pair: 32 mask words (bit l of word r = cell
-// (r, l) stored) and its values contiguous in row-major cell order.  With
-// lane = tile column, row r's values sit at off + prefix(r) + popc(word_r & lanes
-// below), one contiguous run per tile row.
-
-__device__ __forceinline__ int warp_excl_scan(int v, int lane) {
-  int inc = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int n = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += n;
-  }
-  return inc - v;
-}
-
-// Column index of every stored entry (tile-mask format), warp per segment.
-__global__ void k_expand_cols(int64_t n_seg, const int32_t *__restrict__ seg_tile,
-                              const int64_t *__restrict__ seg_off, const uint32_t *__restrict__ mask,
-                              int G, int nT, int32_t *__restrict__ col) {
-  const int lane = threadIdx.x & 31;
-  const unsigned lt = (1u << lane) - 1u;
-  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  for (int64_t s = warp; s < n_seg; s += nwarps) {
-    const unsigned word = mask[s * 32 + lane];
-    const int pre = warp_excl_scan(__popc(word), lane);
-    const int tile = seg_tile[s];
-    const int tu = tile / nT, tv = tile % nT;
-    const int64_t off = seg_off[s];
-    for (int r = 0; r < 32; ++r) {
-      const unsigned wr = __shfl_sync(0xffffffffu, word, r);
-      const int pr = __shfl_sync(0xffffffffu, pre, r);
-      if ((wr >> lane) & 1u) col[off + pr + __popc(wr & lt)] = (tu * 32 + r) * G + tv * 32 + lane;
-    }
-  }
-}
-
 // Column-format degridding kernels; partial sums per row piece into `partial`.
 wproj_status launch_degrid_cols(wproj_plan *p, const float2 *Xt, float2 *partial, cudaStream_t s) {
   const int blocks = (int)std::min<int64_t>(ceil_div(p->n_pieces * 32, 256), 152 * 16);
@@ -231,11 +194,11 @@ wproj_status degrid(wproj_plan *p, const float2 *Xt, float2 *y, cudaStream_t s) 
 wproj_status degrid_into(wproj_plan *p, const float2 *Xt, float2 *partial, float2 *y, cudaStream_t s) {
   {
     ScopedTimer t(p, TC_DEGRID, s);
-    if (p->fmt == WPROJ_INDEX_TILE_MASK) WPROJ_TRY(degrid_mask(p, Xt, partial, s));
+    if (p->fmt == WPROJ_INDEX_TILE_MASK) WPROJ_TRY(degrid_stream(p, Xt, partial, s));
     else WPROJ_TRY(launch_degrid_cols(p, Xt, partial, s));
   }
   ScopedTimer t(p, TC_REDUCE, s);
-  if (p->fmt == WPROJ_INDEX_TILE_MASK) return degrid_mask_reduce(p, partial, y, s);
+  if (p->fmt == WPROJ_INDEX_TILE_MASK) return degrid_stream_reduce(p, partial, y, s);
   k_degrid_reduce<<<ceil_div(p->m, 256), 256, 0, s>>>(p->m, p->row_piece_ptr.as<int32_t>(), partial,
                                                       p->g.value_dtype == WPROJ_VAL_F32 ? nullptr : p->row_scale.as<float>(), y);
   WPROJ_CHECK_LAUNCH("degrid reduce");
@@ -243,7 +206,7 @@ wproj_status degrid_into(wproj_plan *p, const float2 *Xt, float2 *partial, float
 }
 
 int64_t degrid_partials(const wproj_plan *p) {
-  return p->fmt == WPROJ_INDEX_TILE_MASK ? degrid_mask_partials(p) : p->n_pieces;
+  return p->fmt == WPROJ_INDEX_TILE_MASK ? degrid_stream_partials(p) : p->n_pieces;
 }
 
 wproj_status grid(wproj_plan *p, const float2 *y, float2 *Xt2, cudaStream_t s) {
@@ -263,7 +226,7 @@ wproj_status grid(wproj_plan *p, const float2 *y, float2 *Xt2, cudaStream_t s) {
         p->grid_partial.as<float2>());                                                                      \
   } while (0)
     if (p->fmt == WPROJ_INDEX_TILE_MASK) {
-      WPROJ_TRY(grid_mask(p, y, s));
+      WPROJ_TRY(grid_stream(p, y, s));
     } else {
       switch (g.value_dtype) {
         case WPROJ_VAL_F32: LAUNCH_GRID(WPROJ_VAL_F32); break;
@@ -281,15 +244,21 @@ wproj_status grid(wproj_plan *p, const float2 *y, float2 *Xt2, cudaStream_t s) {
   return WPROJ_OK;
 }
 
-wproj_status csr_columns(const wproj_plan *p, int32_t *col_out, cudaStream_t s) {
-  if (p->fmt == WPROJ_INDEX_COLUMNS) {
-    WPROJ_CUDA(cudaMemcpyAsync(col_out, p->col.ptr, sizeof(int32_t) * p->nnz, cudaMemcpyDeviceToDevice, s));
-    return WPROJ_OK;
-  }
-  const int blocks = (int)std::min<int64_t>(ceil_div(p->n_seg * 32, 256), 152 * 32);
-  k_expand_cols<<<std::max(blocks, 1), 256, 0, s>>>(p->n_seg, p->seg_tile.as<int32_t>(), p->seg_off.as<int64_t>(),
-                                                    p->seg_mask.as<uint32_t>(), p->g.G, p->g.nT, col_out);
-  WPROJ_CHECK_LAUNCH("expand columns");
+wproj_status csr_rows(const wproj_plan *p, int64_t k0, int64_t k1, int32_t *col_out, void *val_out,
+                      cudaStream_t s) {
+  if (p->fmt == WPROJ_INDEX_TILE_MASK) return stream_export(p, k0, k1, col_out, val_out, s);
+  int64_t r[2] = {0, 0};
+  WPROJ_CUDA(cudaMemcpyAsync(&r[0], p->row_ptr.as<int64_t>() + k0, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  WPROJ_CUDA(cudaMemcpyAsync(&r[1], p->row_ptr.as<int64_t>() + k1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  WPROJ_CUDA(cudaStreamSynchronize(s));
+  const int64_t n = r[1] - r[0];
+  if (n <= 0) return WPROJ_OK;
+  const size_t vb = p->g.value_dtype == WPROJ_VAL_F32 ? 8 : 4;
+  if (col_out)
+    WPROJ_CUDA(cudaMemcpyAsync(col_out, p->col.as<int32_t>() + r[0], sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+  if (val_out)
+    WPROJ_CUDA(cudaMemcpyAsync(val_out, static_cast<const unsigned char *>(p->val.ptr) + vb * r[0], vb * n,
+                               cudaMemcpyDeviceToDevice, s));
   return WPROJ_OK;
 }
 

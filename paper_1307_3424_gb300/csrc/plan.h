@@ -82,7 +82,10 @@ struct wproj_plan {
   wproj::DevBuf val;         // float2 or 2x16-bit [nnz]
   wproj::DevBuf row_scale;   // float[m]
   int fmt = WPROJ_INDEX_COLUMNS;   // index format of the built G
-  wproj::DevBuf seg_mask;    // uint32[n_seg * 32] (tile-mask format)
+  wproj::DevBuf stream;      // tile-stream records (TILE_MASK format), stream_bytes long
+  int64_t stream_bytes = 0;
+  wproj::DevBuf seg_rec;     // int64[n_seg] byte offset of each segment's record (TILE_MASK)
+  wproj::DevBuf rec_off;     // int64[n_seg+1] byte offset of the records in stream order (TILE_MASK)
   wproj::DevBuf seg_tile;    // int32[n_seg] tile index of each segment
   wproj::DevBuf seg_base;    // int64[m+1] first segment of each row
 
@@ -92,12 +95,12 @@ struct wproj_plan {
   wproj::DevBuf seg_cnt;     // int32[n_seg]
   wproj::DevBuf seg_row;     // int32[n_seg]
   // gridding: segments sorted by tile (rows ascending), chunked by nnz
-  wproj::DevBuf tile_seg;    // int32[n_seg] segment ids
-  wproj::DevBuf seg_meta;    // SegMeta[n_seg] in tile-sorted order
+  wproj::DevBuf seg_meta;    // SegMeta[n_seg] in tile-sorted order (COLUMNS)
   int64_t n_chunks = 0;
   wproj::DevBuf chunk_tile;  // int32[n_chunks]
-  wproj::DevBuf chunk_lo;    // int64[n_chunks]  positions in tile_seg
-  wproj::DevBuf chunk_hi;    // int64[n_chunks]
+  wproj::DevBuf chunk_lo;    // int64[n_chunks]  first position in the tile order (seg_meta /
+                             //                  stream records)
+  wproj::DevBuf chunk_hi;    // int64[n_chunks]  end of the range
   wproj::DevBuf tile_chunk_ptr;  // int32[nT*nT+1]
   // degridding pieces: column format -> entry ranges; tile-mask format -> segment ranges
   int64_t n_pieces = 0;
@@ -112,7 +115,6 @@ struct wproj_plan {
   wproj::DevBuf inter;       // float2[N*G]  between FFT passes
   wproj::DevBuf grid_partial;    // float2[n_chunks * tile^2]
   wproj::DevBuf piece_partial;   // float2[degrid_partials]: per row piece (columns) or segment (mask)
-  wproj::DevBuf dev_err;     // int: error bits raised by kernels (bounded waits)
   wproj::DevBuf xtmp;        // float[N*N]
   wproj::DevBuf ytmp;        // float2[m]
   // solver buffers
@@ -157,14 +159,17 @@ wproj_status phi_forward_fft_into(wproj_plan *p, const float *x, float2 *inter, 
 // ops.cu
 wproj_status degrid(wproj_plan *p, const float2 *Xt, float2 *y, cudaStream_t s);
 wproj_status degrid_into(wproj_plan *p, const float2 *Xt, float2 *partial, float2 *y, cudaStream_t s);
-wproj_status csr_columns(const wproj_plan *p, int32_t *col_out, cudaStream_t s);
+wproj_status csr_rows(const wproj_plan *p, int64_t k0, int64_t k1, int32_t *col_out, void *val_out,
+                      cudaStream_t s);
 int64_t degrid_partials(const wproj_plan *p);   // partial sums degridding needs
 
-// tiles.cu (tile-mask format)
-int64_t degrid_mask_partials(const wproj_plan *p);
-wproj_status degrid_mask(wproj_plan *p, const float2 *Xt, float2 *partial, cudaStream_t s);
-wproj_status degrid_mask_reduce(wproj_plan *p, const float2 *partial, float2 *y, cudaStream_t s);
-wproj_status grid_mask(wproj_plan *p, const float2 *y, cudaStream_t s);
+// tiles.cu (tile-stream records, TILE_MASK format)
+int64_t degrid_stream_partials(const wproj_plan *p);
+wproj_status degrid_stream(wproj_plan *p, const float2 *Xt, float2 *partial, cudaStream_t s);
+wproj_status degrid_stream_reduce(wproj_plan *p, const float2 *partial, float2 *y, cudaStream_t s);
+wproj_status grid_stream(wproj_plan *p, const float2 *y, cudaStream_t s);
+wproj_status stream_export(const wproj_plan *p, int64_t k0, int64_t k1, int32_t *col_out, void *val_out,
+                           cudaStream_t s);
 wproj_status grid(wproj_plan *p, const float2 *y, float2 *Xt2, cudaStream_t s);
 wproj_status apply_phi(wproj_plan *p, const float *x, const float2 *xc, float2 *y, cudaStream_t s);
 wproj_status apply_phi_adj(wproj_plan *p, const float2 *y, float *x_re, float2 *x_cplx,

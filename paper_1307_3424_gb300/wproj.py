@@ -10,7 +10,6 @@ from __future__ import annotations
 
 import ctypes
 import os
-from dataclasses import dataclass
 
 import torch
 
@@ -28,7 +27,7 @@ EXPORTED = [
     "wproj_phi", "wproj_phi_adj", "wproj_phi_cplx", "wproj_solve_bpdn", "wproj_power_norm2",
     "wproj_fft2d", "wproj_set_timing", "wproj_get_stats", "wproj_reset_stats",
     "wproj_dr_defaults", "wproj_last_error", "wproj_version", "wproj_dr_state_get",
-    "wproj_dr_state_set", "wproj_phi_noalloc", "wproj_csr_columns",
+    "wproj_dr_state_set", "wproj_phi_noalloc", "wproj_csr_rows",
 ]
 
 
@@ -48,7 +47,8 @@ class CSR(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int64), ("nnz", ctypes.c_int64), ("n_cols", ctypes.c_int64),
                 ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("val", ctypes.c_void_p),
                 ("row_scale", ctypes.c_void_p), ("value_dtype", ctypes.c_int32),
-                ("index_format", ctypes.c_int32), ("n_seg", ctypes.c_int64), ("tile_mask", ctypes.c_void_p)]
+                ("index_format", ctypes.c_int32), ("n_seg", ctypes.c_int64), ("stream", ctypes.c_void_p),
+                ("stream_bytes", ctypes.c_int64)]
 
 
 class DRParams(ctypes.Structure):
@@ -73,7 +73,7 @@ class Stats(ctypes.Structure):
                 ("t_reduce_ms", ctypes.c_double), ("t_solver_ms", ctypes.c_double),
                 ("n_fft", ctypes.c_int64), ("n_degrid", ctypes.c_int64), ("n_grid", ctypes.c_int64),
                 ("n_reduce", ctypes.c_int64), ("n_solver", ctypes.c_int64),
-                ("launches", ctypes.c_int64), ("device_errors", ctypes.c_int32)]
+                ("launches", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -102,7 +102,7 @@ def lib() -> ctypes.CDLL:
         "wproj_phi_adj": [vp, vp, vp, vp, vp],
         "wproj_phi_cplx": [vp, vp, vp, vp],
         "wproj_phi_noalloc": [vp, vp, vp, vp],
-        "wproj_csr_columns": [vp, vp, vp],
+        "wproj_csr_rows": [vp, i64, i64, vp, vp, vp],
         "wproj_solve_bpdn": [vp, vp, dbl, P(DRParams), vp, P(SolveInfo), vp],
         "wproj_power_norm2": [vp, i32, P(dbl), vp],
         "wproj_fft2d": [vp, vp, i32, i32, i32, vp],
@@ -158,18 +158,61 @@ def dr_defaults() -> DRParams:
     return p
 
 
-@dataclass
 class CSRView:
-    m: int
-    nnz: int
-    n_cols: int
-    row_ptr: torch.Tensor
-    col: torch.Tensor
-    val: torch.Tensor          # complex64 (f32) or (nnz, 2) bf16/f16
-    row_scale: torch.Tensor | None
-    value_dtype: str
-    index_format: str = "columns"
-    n_seg: int = 0
+    """G in CSR terms (valid until the next build or close of its plan).
+
+    row_ptr is a zero-copy view.  COLUMNS format: `col` / `val` are zero-copy
+    views of the plan's arrays.  TILE_MASK format (tile stream): `rows(k0, k1)`
+    exports rows on demand; `col` / `val` export every row on first access.
+    Values are complex64 (f32) or (nnz, 2) bf16 / f16 scaled by `row_scale`.
+    """
+
+    def __init__(self, plan: "Plan", c: CSR):
+        self._plan = plan
+        self.m, self.nnz, self.n_cols, self.n_seg = int(c.m), int(c.nnz), int(c.n_cols), int(c.n_seg)
+        self.value_dtype = {0: "f32", 1: "bf16", 2: "f16"}[c.value_dtype]
+        self.index_format = {1: "columns", 2: "mask"}[c.index_format]
+        self.stream_bytes = int(c.stream_bytes)
+        self._dev = torch.device("cuda", torch.cuda.current_device())
+        self.row_ptr = torch.as_tensor(_CAI(c.row_ptr, (self.m + 1,), "<i8"), device=self._dev)
+        self.row_scale = None
+        if c.value_dtype != 0:
+            self.row_scale = torch.as_tensor(_CAI(c.row_scale, (self.m,), "<f4"), device=self._dev)
+        self._col = self._val = None
+        if self.index_format == "columns":
+            self._col = torch.as_tensor(_CAI(c.col, (self.nnz,), "<i4"), device=self._dev)
+            self._val = self._val_view(torch.as_tensor(_CAI(c.val, (self.nnz, 2), "<f4" if c.value_dtype == 0
+                                                            else "<i2"), device=self._dev))
+
+    def _val_view(self, raw: torch.Tensor) -> torch.Tensor:
+        if self.value_dtype == "f32":
+            return torch.view_as_complex(raw)
+        return raw.view(torch.bfloat16 if self.value_dtype == "bf16" else torch.float16)
+
+    def rows(self, k0: int, k1: int):
+        """(col, val) of rows [k0, k1) in CSR order, fresh device tensors."""
+        rp = self.row_ptr
+        n = int(rp[k1].item() - rp[k0].item()) if k1 > k0 else 0
+        col = torch.empty(max(n, 1), dtype=torch.int32, device=self._dev)[:n]
+        raw = torch.empty((max(n, 1), 2), dtype=torch.float32 if self.value_dtype == "f32" else torch.int16,
+                          device=self._dev)[:n]
+        _check(lib().wproj_csr_rows(self._plan._h, int(k0), int(k1), ctypes.c_void_p(col.data_ptr()),
+                                    ctypes.c_void_p(raw.data_ptr()), _stream(None)))
+        return col, self._val_view(raw)
+
+    def _export_all(self):
+        if self._col is None:
+            self._col, self._val = self.rows(0, self.m)
+
+    @property
+    def col(self) -> torch.Tensor:
+        self._export_all()
+        return self._col
+
+    @property
+    def val(self) -> torch.Tensor:
+        self._export_all()
+        return self._val
 
 
 class Plan:
@@ -216,28 +259,10 @@ class Plan:
         return out
 
     def csr(self) -> CSRView:
-        """Zero-copy views of G (valid until the next build or close)."""
+        """View of G (see CSRView)."""
         c = CSR()
         _check(lib().wproj_get_csr(self._h, ctypes.byref(c)))
-        dev = torch.device("cuda", torch.cuda.current_device())
-        rp = torch.as_tensor(_CAI(c.row_ptr, (c.m + 1,), "<i8"), device=dev)
-        nnz = max(int(c.nnz), 0)
-        if c.index_format == INDEX_FORMAT["columns"]:
-            col = torch.as_tensor(_CAI(c.col, (nnz,), "<i4"), device=dev)
-        else:   # tile masks: expand to a fresh column array
-            col = torch.empty(max(nnz, 1), dtype=torch.int32, device=dev)[:nnz]
-            _check(lib().wproj_csr_columns(self._h, ctypes.c_void_p(col.data_ptr()), _stream(None)))
-        if c.value_dtype == 0:
-            val = torch.as_tensor(_CAI(c.val, (nnz, 2), "<f4"), device=dev)
-            val = torch.view_as_complex(val)
-            rs = None
-        else:
-            val = torch.as_tensor(_CAI(c.val, (nnz, 2), "<i2"), device=dev)
-            val = val.view(torch.bfloat16 if c.value_dtype == 1 else torch.float16)
-            rs = torch.as_tensor(_CAI(c.row_scale, (c.m,), "<f4"), device=dev)
-        name = {0: "f32", 1: "bf16", 2: "f16"}[c.value_dtype]
-        fmt = {1: "columns", 2: "mask"}[c.index_format]
-        return CSRView(int(c.m), int(c.nnz), int(c.n_cols), rp, col, val, rs, name, fmt, int(c.n_seg))
+        return CSRView(self, c)
 
     # ---- Part II
     def phi(self, x: torch.Tensor, y: torch.Tensor | None = None, stream=None) -> torch.Tensor:

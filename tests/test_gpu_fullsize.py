@@ -39,13 +39,13 @@ def test_sampled_rows_match_oracle(built):
     plan, geo, prob, rows = built["plan"], built["geo"], built["prob"], built["rows"]
     e = built["wl"].e
     c = plan.csr()
-    rp = c.row_ptr.cpu().numpy()
     G = geo.G
     S = G
     num = den = 0.0
     for k in rows:
-        col = c.col[rp[k]:rp[k + 1]].cpu().numpy()
-        vg = c.val[rp[k]:rp[k + 1]].cpu().numpy().astype(np.complex128)
+        col_k, val_k = c.rows(k, k + 1)
+        col = col_k.cpu().numpy()
+        vg = val_k.cpu().numpy().astype(np.complex128)
         assert np.unique(col).size == col.size
         K, j0u, j0v = O.kernel_box(geo, *prob.uvw[k], S)
         su = ((col // G - j0u + G // 2) % G) - G // 2

@@ -247,14 +247,27 @@ def test_index_formats_build_and_operators(wp, N, M, e, box, vdt):
     yv = rng.standard_normal(M) + 1j * rng.standard_normal(M)
     xg = torch.from_numpy(x.astype(np.float32)).to(dev())
     yg = torch.from_numpy(yv.astype(np.complex64)).to(dev())
-    out = {}
+    out, exported = {}, {}
     for fmt in ("columns", "mask"):
         plan = wp.Plan(N, L, box=box or "G", value_dtype=vdt, index_format=fmt)
         plan.build_kernels(torch.from_numpy(uvw).to(dev()), e)
-        assert plan.csr().index_format == fmt
+        c = plan.csr()
+        assert c.index_format == fmt
         check_build(plan, geo, uvw, e, box, tol=1e-5 if vdt == "f32" else 8e-3)
         out[fmt] = (plan.phi(xg).cpu().numpy(), plan.phi_adj(yg, complex_out=True).cpu().numpy())
+        # row-range export agrees with the whole-matrix view, ragged ranges included
+        col, val = c.col.cpu(), torch.view_as_real(c.val).cpu() if vdt == "f32" else c.val.cpu()
+        rp = c.row_ptr.cpu().numpy()
+        for k0, k1 in ((0, 1), (3, 17), (M - 5, M), (7, 7)):
+            ck, vk = c.rows(k0, k1)
+            vk = torch.view_as_real(vk) if vdt == "f32" else vk
+            assert torch.equal(ck.cpu(), col[rp[k0]:rp[k1]])
+            assert torch.equal(vk.cpu(), val[rp[k0]:rp[k1]])
+        exported[fmt] = (col, val)
         plan.close()
+    # the same G: identical columns and stored values in CSR order
+    assert torch.equal(exported["columns"][0], exported["mask"][0])
+    assert torch.equal(exported["columns"][1], exported["mask"][1])
     for a, b in zip(out["columns"], out["mask"]):
         assert np.linalg.norm(a - b) <= 1e-6 * np.linalg.norm(a)
     if e == 1.0 and vdt == "f32":

@@ -56,16 +56,16 @@ def test_precision_form_against_oracle(case, vdt):
     plan = wp.Plan(wl.N, prob.L, box="rule", value_dtype=vdt)
     plan.build_kernels(torch.from_numpy(prob.uvw).to(dev), wl.e)
     c = plan.csr()
-    rp = c.row_ptr.cpu().numpy()
     G = geo.G
     num = den = 0.0
     for k in case["rows"]:
         S, _, _, (K, j0u, j0v) = case["orows"][k]
-        col = c.col[rp[k]:rp[k + 1]].cpu().numpy()
+        col_k, val_k = c.rows(k, k + 1)
+        col = col_k.cpu().numpy()
         if vdt == "f32":
-            vg = c.val[rp[k]:rp[k + 1]].cpu().numpy().astype(np.complex128)
+            vg = val_k.cpu().numpy().astype(np.complex128)
         else:
-            v = c.val[rp[k]:rp[k + 1]].float().cpu().numpy()
+            v = val_k.float().cpu().numpy()
             vg = (v[:, 0] + 1j * v[:, 1]) * float(c.row_scale[k])
         su = ((col // G - j0u + G // 2) % G) - G // 2
         sv = ((col % G - j0v + G // 2) % G) - G // 2
