@@ -261,6 +261,70 @@ void wproj_dr_defaults(wproj_dr_params *prm);
 const char *wproj_last_error(void);
 const char *wproj_version(void);
 
+/* ---- batches of independent problems ------------------------------------------
+ * Many imaging problems of uneven N and M (each a full Eq. 7 problem with its own
+ * Phi, Section 3) held in one object.  Every stage of Phi, Phi^H and the
+ * Douglas-Rachford iteration runs as one launch for all problems, and one DR
+ * iteration is captured as a CUDA graph and replayed.  Batches store G with
+ * column indices in complex64 (value_dtype F32; index_format AUTO or COLUMNS).
+ *
+ * Concatenated layouts (problems in order p = 0 .. n-1):
+ *   images        x_p is N_p x N_p floats at offset sum_{q<p} N_q^2
+ *   visibilities  y_p is m_p complex64 at offset sum_{q<p} m_q
+ *   uvw           m_p x 3 doubles at offset 3 sum_{q<p} m_q
+ * All arrays are caller-owned device pointers unless stated. */
+typedef struct wproj_batch wproj_batch;
+
+/* Work split of the batch operators: degridding row pieces of <= piece entries,
+ * gridding chunks of about chunk entries of one grid tile. */
+typedef struct {
+  int64_t piece;
+  int64_t chunk;
+  double degrid_ms;     /* wproj_batch_tune: measured time of the chosen schedules */
+  double grid_ms;
+} wproj_batch_schedule;
+
+typedef struct {
+  int32_t n_problems;
+  int64_t m;            /* visibilities of all problems */
+  int64_t pixels;       /* image pixels of all problems */
+  int64_t nnz;          /* stored entries of all G */
+  int64_t n_pieces, n_chunks, piece, chunk;
+  int64_t launches;     /* kernels launched by batch operator and solver calls */
+  int64_t iter_launches;  /* kernels in one captured Douglas-Rachford iteration */
+} wproj_batch_info;
+
+/* n problems (1 <= n <= 65535) with geometries descs[n] (host); each is validated
+ * as by wproj_plan_create.  Other value dtypes or TILE_MASK: WPROJ_ERR_UNSUPPORTED. */
+wproj_status wproj_batch_create(wproj_batch **out, int32_t n, const wproj_grid_desc *descs);
+wproj_status wproj_batch_destroy(wproj_batch *b);
+
+/* Part I for every problem: uvw concatenated as above (device), m[n] rows per
+ * problem (host), energy fraction e as in wproj_build_kernels.  Synchronous.
+ * Sets a default schedule (piece 1024, chunk 8192). */
+wproj_status wproj_batch_build(wproj_batch *b, const double *uvw, const int64_t *m, double e, void *stream);
+
+/* Times candidate schedules on this batch (pieces 256 .. 16384 entries, chunks
+ * 2048 .. 65536 entries), keeps the fastest of each; out (host) may be NULL.
+ * Synchronous. */
+wproj_status wproj_batch_tune(wproj_batch *b, wproj_batch_schedule *out, void *stream);
+/* Sets a schedule explicitly (piece, chunk >= 32).  Synchronous. */
+wproj_status wproj_batch_set_schedule(wproj_batch *b, int64_t piece, int64_t chunk, void *stream);
+
+/* y = Phi x and x_re = Re Phi^H y for every problem (layouts above). */
+wproj_status wproj_batch_phi(wproj_batch *b, const float *x, void *y, void *stream);
+wproj_status wproj_batch_phi_adj(wproj_batch *b, const void *y, float *x_re, void *stream);
+
+/* Eq. 7 for every problem by Douglas-Rachford as wproj_solve_bpdn, with eps[n]
+ * (host) per problem and one parameter set; ||Phi_p||^2 is always estimated per
+ * problem by prm->power_iters power iterations (prm->phi_norm2 is ignored).
+ * prm->resume continues the batch's state.  The iterations replay a captured
+ * CUDA graph (recaptured when y, inner_iters or lambda change).  x_out: all
+ * images, concatenated. */
+wproj_status wproj_batch_solve_bpdn(wproj_batch *b, const void *y, const double *eps, const wproj_dr_params *prm,
+                                    float *x_out, void *stream);
+wproj_status wproj_batch_get_info(const wproj_batch *b, wproj_batch_info *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -604,8 +604,7 @@ k_emit(const float2 *__restrict__ K, int S, const int32_t *__restrict__ ids,
 
 __global__ void k_row_ptr(int64_t m, const int64_t *__restrict__ seg_base,
                           const int64_t *__restrict__ seg_off, const int32_t *__restrict__ ntile,
-                          int64_t n_seg, int64_t nnz, int64_t piece, int fmt,
-                          int64_t *__restrict__ row_ptr, int32_t *__restrict__ npieces) {
+                          int64_t n_seg, int64_t nnz, int64_t *__restrict__ row_ptr) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k > m) return;
   if (k == m) { row_ptr[m] = nnz; return; }
@@ -614,8 +613,13 @@ __global__ void k_row_ptr(int64_t m, const int64_t *__restrict__ seg_base,
   const int64_t end = (k + 1 < m) ? ((seg_base[k + 1] < n_seg) ? seg_off[seg_base[k + 1]] : nnz) : nnz;
   row_ptr[k] = start;
   (void)ntile;
-  // row pieces of the column-format degridding (the tile stream has none)
-  npieces[k] = fmt == WPROJ_INDEX_TILE_MASK ? 0 : int32_t(i64max(1, (end - start + piece - 1) / piece));
+  (void)end;
+}
+
+__global__ void k_npieces(int64_t m, const int64_t *__restrict__ row_ptr, int64_t piece,
+                          int32_t *__restrict__ npieces) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k < m) npieces[k] = int32_t(i64max(1, (row_ptr[k + 1] - row_ptr[k] + piece - 1) / piece));
 }
 
 // Row pieces of the column-format degridding: ranges of <= piece entries.
@@ -720,6 +724,59 @@ __global__ void k_chunk_fill(int n_tiles, const int64_t *__restrict__ tile_ptr,
 
 }  // namespace
 
+wproj_status make_row_pieces(int64_t m, const int64_t *row_ptr, int64_t piece, DevBuf &piece_row, DevBuf &piece_lo,
+                             DevBuf &piece_len, DevBuf &row_piece_ptr, int64_t *n_pieces, cudaStream_t s) {
+  DevBuf npc, pbase;
+  WPROJ_TRY(npc.alloc(sizeof(int32_t) * std::max<int64_t>(1, m)));
+  WPROJ_TRY(pbase.alloc(sizeof(int64_t) * (m + 1)));
+  k_npieces<<<ceil_div(m, 256), 256, 0, s>>>(m, row_ptr, piece, npc.as<int32_t>());
+  WPROJ_CHECK_LAUNCH("piece counts");
+  WPROJ_TRY(exclusive_scan_i32_to_i64(npc.as<int32_t>(), pbase.as<int64_t>(), m, s));
+  int64_t lb = 0;
+  int32_t ln = 0;
+  WPROJ_CUDA(cudaMemcpyAsync(&lb, pbase.as<int64_t>() + (m - 1), sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  WPROJ_CUDA(cudaMemcpyAsync(&ln, npc.as<int32_t>() + (m - 1), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  WPROJ_CUDA(cudaStreamSynchronize(s));
+  *n_pieces = lb + ln;
+  if (*n_pieces >= (int64_t(1) << 31)) return fail(WPROJ_ERR_UNSUPPORTED, "too many row pieces");
+  WPROJ_TRY(piece_row.alloc(sizeof(int32_t) * *n_pieces));
+  WPROJ_TRY(piece_lo.alloc(sizeof(int64_t) * *n_pieces));
+  WPROJ_TRY(piece_len.alloc(sizeof(int32_t) * *n_pieces));
+  WPROJ_TRY(row_piece_ptr.alloc(sizeof(int32_t) * (m + 1)));
+  k_pieces<<<ceil_div(m + 1, 256), 256, 0, s>>>(m, row_ptr, pbase.as<int64_t>(), piece_row.as<int32_t>(),
+                                                piece_lo.as<int64_t>(), piece_len.as<int32_t>(),
+                                                row_piece_ptr.as<int32_t>(), *n_pieces, piece);
+  WPROJ_CHECK_LAUNCH("pieces");
+  return WPROJ_OK;
+}
+
+wproj_status make_tile_chunks(int n_tiles, const int64_t *tptr, const int64_t *cum, int64_t n_seg, int64_t nnz,
+                              int64_t chunk, DevBuf &chunk_tile, DevBuf &chunk_lo, DevBuf &chunk_hi,
+                              DevBuf &tile_chunk_ptr, int64_t *n_chunks, cudaStream_t s) {
+  DevBuf nch, chbase;
+  WPROJ_TRY(nch.alloc(sizeof(int32_t) * n_tiles));
+  WPROJ_TRY(chbase.alloc(sizeof(int64_t) * (n_tiles + 1)));
+  k_tile_chunks<<<ceil_div(n_tiles, 256), 256, 0, s>>>(n_tiles, tptr, cum, n_seg, nnz, chunk, nch.as<int32_t>());
+  WPROJ_CHECK_LAUNCH("tile chunks");
+  WPROJ_TRY(exclusive_scan_i32_to_i64(nch.as<int32_t>(), chbase.as<int64_t>(), n_tiles, s));
+  int64_t lb = 0;
+  int32_t ln = 0;
+  WPROJ_CUDA(cudaMemcpyAsync(&lb, chbase.as<int64_t>() + (n_tiles - 1), sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  WPROJ_CUDA(cudaMemcpyAsync(&ln, nch.as<int32_t>() + (n_tiles - 1), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  WPROJ_CUDA(cudaStreamSynchronize(s));
+  *n_chunks = lb + ln;
+  WPROJ_TRY(chunk_tile.alloc(sizeof(int32_t) * *n_chunks));
+  WPROJ_TRY(chunk_lo.alloc(sizeof(int64_t) * *n_chunks));
+  WPROJ_TRY(chunk_hi.alloc(sizeof(int64_t) * *n_chunks));
+  WPROJ_TRY(tile_chunk_ptr.alloc(sizeof(int32_t) * (n_tiles + 1)));
+  k_chunk_fill<<<ceil_div(n_tiles + 1, 256), 256, 0, s>>>(n_tiles, tptr, cum, n_seg, nnz, chbase.as<int64_t>(),
+                                                          chunk_tile.as<int32_t>(), chunk_lo.as<int64_t>(),
+                                                          chunk_hi.as<int64_t>(), tile_chunk_ptr.as<int32_t>(),
+                                                          *n_chunks, chunk);
+  WPROJ_CHECK_LAUNCH("chunk fill");
+  return WPROJ_OK;
+}
+
 wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, double e, cudaStream_t s) {
   auto t_start = std::chrono::steady_clock::now();
   const GridGeom &g = p->g;
@@ -813,7 +870,7 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
   const int vdt = g.value_dtype;
   const int vb = vdt == WPROJ_VAL_F32 ? 8 : 4;
   const int n_tiles = g.nT * g.nT;
-  DevBuf d_pieces_n, tile_seg, tptr;
+  DevBuf tile_seg, tptr;
 
   for (int phase = 1; phase <= 2; ++phase) {
     if (phase == 2) {
@@ -877,10 +934,8 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
         WPROJ_TRY(p->val.alloc(int64_t(vb) * std::max<int64_t>(1, p->nnz)));
       }
       WPROJ_TRY(p->row_ptr.alloc(sizeof(int64_t) * (m + 1)));
-      WPROJ_TRY(d_pieces_n.alloc(sizeof(int32_t) * (m + 1)));
       k_row_ptr<<<ceil_div(m + 1, 256), 256, 0, s>>>(m, d_segbase.as<int64_t>(), p->seg_off.as<int64_t>(),
-                                                     d_ntile.as<int32_t>(), n_seg, p->nnz, degrid_piece(p->nnz),
-                                                     p->fmt, p->row_ptr.as<int64_t>(), d_pieces_n.as<int32_t>());
+                                                     d_ntile.as<int32_t>(), n_seg, p->nnz, p->row_ptr.as<int64_t>());
       WPROJ_CHECK_LAUNCH("row ptr");
     }
     for (int c = 0; c < 9; ++c) {
@@ -969,31 +1024,16 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
     p->row_piece_ptr.release();
     WPROJ_TRY(p->piece_partial.alloc(sizeof(float2) * std::max<int64_t>(1, kStreamWarps * n_seg)));
   } else {
-    DevBuf pbase;
-    WPROJ_TRY(pbase.alloc(sizeof(int64_t) * (m + 1)));
-    WPROJ_TRY(exclusive_scan_i32_to_i64(d_pieces_n.as<int32_t>(), pbase.as<int64_t>(), m, s));
-    int64_t lb = 0;
-    int32_t ln = 0;
-    WPROJ_CUDA(cudaMemcpy(&lb, pbase.as<int64_t>() + (m - 1), sizeof(int64_t), cudaMemcpyDeviceToHost));
-    WPROJ_CUDA(cudaMemcpy(&ln, d_pieces_n.as<int32_t>() + (m - 1), sizeof(int32_t), cudaMemcpyDeviceToHost));
-    p->n_pieces = lb + ln;
-    WPROJ_TRY(p->piece_row.alloc(sizeof(int32_t) * p->n_pieces));
-    WPROJ_TRY(p->piece_lo.alloc(sizeof(int64_t) * p->n_pieces));
-    WPROJ_TRY(p->piece_len.alloc(sizeof(int32_t) * p->n_pieces));
-    WPROJ_TRY(p->row_piece_ptr.alloc(sizeof(int32_t) * (m + 1)));
+    WPROJ_TRY(make_row_pieces(m, p->row_ptr.as<int64_t>(), degrid_piece(p->nnz), p->piece_row, p->piece_lo,
+                              p->piece_len, p->row_piece_ptr, &p->n_pieces, s));
     WPROJ_TRY(p->piece_partial.alloc(sizeof(float2) * std::max<int64_t>(1, p->n_pieces)));
-    k_pieces<<<ceil_div(m + 1, 256), 256, 0, s>>>(m, p->row_ptr.as<int64_t>(), pbase.as<int64_t>(),
-                                                  p->piece_row.as<int32_t>(), p->piece_lo.as<int64_t>(),
-                                                  p->piece_len.as<int32_t>(), p->row_piece_ptr.as<int32_t>(),
-                                                  p->n_pieces, degrid_piece(p->nnz));
-    WPROJ_CHECK_LAUNCH("pieces");
   }
 
   // ---- gridding: chunks of one tile's segments (tile order), balanced by entries
   {
     const bool rec = p->fmt == WPROJ_INDEX_TILE_MASK;
     const int64_t chunk = grid_chunk(p->nnz);
-    DevBuf cntsorted, cum, nch, chbase;
+    DevBuf cntsorted, cum;
     WPROJ_TRY(cntsorted.alloc(sizeof(int32_t) * std::max<int64_t>(1, n_seg)));
     WPROJ_TRY(cum.alloc(sizeof(int64_t) * std::max<int64_t>(1, n_seg)));
     if (!rec) WPROJ_TRY(p->seg_meta.alloc(sizeof(SegMeta) * std::max<int64_t>(1, n_seg)));
@@ -1005,26 +1045,8 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
       WPROJ_CHECK_LAUNCH("gather cnt");
       WPROJ_TRY(exclusive_scan_i32_to_i64(cntsorted.as<int32_t>(), cum.as<int64_t>(), n_seg, s));
     }
-    WPROJ_TRY(nch.alloc(sizeof(int32_t) * n_tiles));
-    WPROJ_TRY(chbase.alloc(sizeof(int64_t) * (n_tiles + 1)));
-    k_tile_chunks<<<ceil_div(n_tiles, 256), 256, 0, s>>>(n_tiles, tptr.as<int64_t>(), cum.as<int64_t>(), n_seg,
-                                                         p->nnz, chunk, nch.as<int32_t>());
-    WPROJ_CHECK_LAUNCH("tile chunks");
-    WPROJ_TRY(exclusive_scan_i32_to_i64(nch.as<int32_t>(), chbase.as<int64_t>(), n_tiles, s));
-    int64_t lb = 0;
-    int32_t ln = 0;
-    WPROJ_CUDA(cudaMemcpy(&lb, chbase.as<int64_t>() + (n_tiles - 1), sizeof(int64_t), cudaMemcpyDeviceToHost));
-    WPROJ_CUDA(cudaMemcpy(&ln, nch.as<int32_t>() + (n_tiles - 1), sizeof(int32_t), cudaMemcpyDeviceToHost));
-    p->n_chunks = lb + ln;
-    WPROJ_TRY(p->chunk_tile.alloc(sizeof(int32_t) * p->n_chunks));
-    WPROJ_TRY(p->chunk_lo.alloc(sizeof(int64_t) * p->n_chunks));
-    WPROJ_TRY(p->chunk_hi.alloc(sizeof(int64_t) * p->n_chunks));
-    WPROJ_TRY(p->tile_chunk_ptr.alloc(sizeof(int32_t) * (n_tiles + 1)));
-    k_chunk_fill<<<ceil_div(n_tiles + 1, 256), 256, 0, s>>>(n_tiles, tptr.as<int64_t>(), cum.as<int64_t>(), n_seg,
-                                                            p->nnz, chbase.as<int64_t>(), p->chunk_tile.as<int32_t>(),
-                                                            p->chunk_lo.as<int64_t>(), p->chunk_hi.as<int64_t>(),
-                                                            p->tile_chunk_ptr.as<int32_t>(), p->n_chunks, chunk);
-    WPROJ_CHECK_LAUNCH("chunk fill");
+    WPROJ_TRY(make_tile_chunks(n_tiles, tptr.as<int64_t>(), cum.as<int64_t>(), n_seg, p->nnz, chunk, p->chunk_tile,
+                               p->chunk_lo, p->chunk_hi, p->tile_chunk_ptr, &p->n_chunks, s));
     WPROJ_TRY(p->grid_partial.alloc(sizeof(float2) * size_t(p->n_chunks) * g.tile * g.tile));
   }
   WPROJ_TRY(p->ytmp.alloc(sizeof(float2) * m));

@@ -45,6 +45,28 @@ __device__ __forceinline__ float abs2_rn(float2 z) {
   return __fadd_rn(__fmul_rn(z.x, z.x), __fmul_rn(z.y, z.y));
 }
 
+// ---- FP64 block reductions (fixed order: bit-reproducible) ---------------------
+__device__ __forceinline__ double warp_sum_d(double v) {
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// sum over a block of T threads; the result is valid in thread 0
+template <int T>
+__device__ __forceinline__ double block_sum_d(double v) {
+  __shared__ double red[T / 32];
+  v = warp_sum_d(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0;
+  if (threadIdx.x < 32) {
+    t = (threadIdx.x < T / 32) ? red[threadIdx.x] : 0.0;
+    t = warp_sum_d(t);
+  }
+  __syncthreads();
+  return t;
+}
+
 // ---- error state ------------------------------------------------------------
 void set_error(const std::string &msg);
 wproj_status fail(wproj_status st, const std::string &msg);

@@ -42,15 +42,18 @@ __device__ __forceinline__ int img_to_pad(int p, int N, int G) {
 
 // ---- Phi: F Z A --------------------------------------------------------------
 
+// Each pass is a device body (block `blk` of one transform set) called by a
+// kernel for one plan and by a kernel for a batch of same-size problems
+// (blockIdx.y = problem of the size class, offsets from its BProb entry).
 template <int LOGN>
-__global__ void __launch_bounds__(RowCfg<LOGN>::T)
-k_phi_fwd_rows(const float *__restrict__ x, const float2 *__restrict__ xc,
-               const float *__restrict__ inv_a, int N, float2 *__restrict__ inter,
-               const float2 *__restrict__ tw) {
+__device__ __forceinline__ void phi_fwd_rows_body(const float *__restrict__ x, const float2 *__restrict__ xc,
+                                                  const float *__restrict__ inv_a, int N,
+                                                  float2 *__restrict__ inter, const float2 *__restrict__ tw,
+                                                  int blk) {
   using Cfg = RowCfg<LOGN>;
   constexpr int G = 1 << LOGN;
   extern __shared__ float2 sm[];
-  const int p0 = blockIdx.x * Cfg::C;
+  const int p0 = blk * Cfg::C;
   for (int idx = threadIdx.x; idx < Cfg::C * G; idx += Cfg::T) {
     const int c = idx / G, Q = idx % G;
     const int p = p0 + c;
@@ -75,13 +78,27 @@ k_phi_fwd_rows(const float *__restrict__ x, const float2 *__restrict__ xc,
 }
 
 template <int LOGN>
-__global__ void __launch_bounds__(ColCfg<LOGN>::T)
-k_phi_fwd_cols(const float2 *__restrict__ inter, int N, float2 *__restrict__ Xt, float scale,
-               const float2 *__restrict__ tw) {
+__global__ void __launch_bounds__(RowCfg<LOGN>::T)
+k_phi_fwd_rows(const float *__restrict__ x, const float2 *__restrict__ xc, const float *__restrict__ inv_a, int N,
+               float2 *__restrict__ inter, const float2 *__restrict__ tw) {
+  phi_fwd_rows_body<LOGN>(x, xc, inv_a, N, inter, tw, blockIdx.x);
+}
+
+template <int LOGN>
+__global__ void __launch_bounds__(RowCfg<LOGN>::T)
+k_bphi_fwd_rows(const BProb *__restrict__ tab, const int32_t *__restrict__ plist, const float *__restrict__ x,
+                const float *__restrict__ inv_a, float2 *__restrict__ inter, const float2 *__restrict__ tw) {
+  const BProb P = tab[plist[blockIdx.y]];
+  phi_fwd_rows_body<LOGN>(x + P.img_off, nullptr, inv_a + P.inva_off, P.N, inter + P.inter_off, tw, blockIdx.x);
+}
+
+template <int LOGN>
+__device__ __forceinline__ void phi_fwd_cols_body(const float2 *__restrict__ inter, int N, float2 *__restrict__ Xt,
+                                                  float scale, const float2 *__restrict__ tw, int blk) {
   using Cfg = ColCfg<LOGN>;
   constexpr int G = 1 << LOGN;
   extern __shared__ float2 sm[];
-  const int Q0 = blockIdx.x * Cfg::C;
+  const int Q0 = blk * Cfg::C;
   for (int idx = threadIdx.x; idx < Cfg::C * G; idx += Cfg::T) {
     const int P = idx / Cfg::C, c = idx % Cfg::C;
     const int p = pad_to_img(P, N, G);
@@ -97,16 +114,30 @@ k_phi_fwd_cols(const float2 *__restrict__ inter, int N, float2 *__restrict__ Xt,
   }
 }
 
-// ---- Phi^H: A Z^H F^H -----------------------------------------------------------
+template <int LOGN>
+__global__ void __launch_bounds__(ColCfg<LOGN>::T)
+k_phi_fwd_cols(const float2 *__restrict__ inter, int N, float2 *__restrict__ Xt, float scale,
+               const float2 *__restrict__ tw) {
+  phi_fwd_cols_body<LOGN>(inter, N, Xt, scale, tw, blockIdx.x);
+}
 
 template <int LOGN>
 __global__ void __launch_bounds__(ColCfg<LOGN>::T)
-k_phi_adj_cols(const float2 *__restrict__ Xt2, int N, float2 *__restrict__ inter,
-               const float2 *__restrict__ tw) {
+k_bphi_fwd_cols(const BProb *__restrict__ tab, const int32_t *__restrict__ plist, const float2 *__restrict__ inter,
+                float2 *__restrict__ Xt, const float2 *__restrict__ tw) {
+  const BProb P = tab[plist[blockIdx.y]];
+  phi_fwd_cols_body<LOGN>(inter + P.inter_off, P.N, Xt + P.grid_off, 1.0f / P.G, tw, blockIdx.x);
+}
+
+// ---- Phi^H: A Z^H F^H -----------------------------------------------------------
+
+template <int LOGN>
+__device__ __forceinline__ void phi_adj_cols_body(const float2 *__restrict__ Xt2, int N, float2 *__restrict__ inter,
+                                                  const float2 *__restrict__ tw, int blk) {
   using Cfg = ColCfg<LOGN>;
   constexpr int G = 1 << LOGN;
   extern __shared__ float2 sm[];
-  const int Q0 = blockIdx.x * Cfg::C;
+  const int Q0 = blk * Cfg::C;
   for (int idx = threadIdx.x; idx < Cfg::C * G; idx += Cfg::T) {
     const int P = idx / Cfg::C, c = idx % Cfg::C;
     sm[c * Cfg::LD + P] = (Q0 + c < G) ? Xt2[int64_t(P) * G + Q0 + c] : make_float2(0.f, 0.f);
@@ -119,16 +150,30 @@ k_phi_adj_cols(const float2 *__restrict__ Xt2, int N, float2 *__restrict__ inter
   }
 }
 
+template <int LOGN>
+__global__ void __launch_bounds__(ColCfg<LOGN>::T)
+k_phi_adj_cols(const float2 *__restrict__ Xt2, int N, float2 *__restrict__ inter, const float2 *__restrict__ tw) {
+  phi_adj_cols_body<LOGN>(Xt2, N, inter, tw, blockIdx.x);
+}
+
+template <int LOGN>
+__global__ void __launch_bounds__(ColCfg<LOGN>::T)
+k_bphi_adj_cols(const BProb *__restrict__ tab, const int32_t *__restrict__ plist, const float2 *__restrict__ Xt2,
+                float2 *__restrict__ inter, const float2 *__restrict__ tw) {
+  const BProb P = tab[plist[blockIdx.y]];
+  phi_adj_cols_body<LOGN>(Xt2 + P.grid_off, P.N, inter + P.inter_off, tw, blockIdx.x);
+}
+
 // mode 0: x_re = Re(v) s (and x_c = v s when given); mode 1: x_re = z - Re(v) s
 template <int LOGN>
-__global__ void __launch_bounds__(RowCfg<LOGN>::T)
-k_phi_adj_rows(const float2 *__restrict__ inter, const float *__restrict__ inv_a, int N,
-               float scale, float *__restrict__ x_re, float2 *__restrict__ x_c,
-               const float *__restrict__ z, int mode, const float2 *__restrict__ tw) {
+__device__ __forceinline__ void phi_adj_rows_body(const float2 *__restrict__ inter, const float *__restrict__ inv_a,
+                                                  int N, float scale, float *__restrict__ x_re,
+                                                  float2 *__restrict__ x_c, const float *__restrict__ z, int mode,
+                                                  const float2 *__restrict__ tw, int blk) {
   using Cfg = RowCfg<LOGN>;
   constexpr int G = 1 << LOGN;
   extern __shared__ float2 sm[];
-  const int p0 = blockIdx.x * Cfg::C;
+  const int p0 = blk * Cfg::C;
   for (int idx = threadIdx.x; idx < Cfg::C * G; idx += Cfg::T) {
     const int c = idx / G, Q = idx % G;
     const int p = p0 + c;
@@ -150,6 +195,24 @@ k_phi_adj_rows(const float2 *__restrict__ inter, const float *__restrict__ inv_a
       x_re[o] = z[o] - v.x * s;
     }
   }
+}
+
+template <int LOGN>
+__global__ void __launch_bounds__(RowCfg<LOGN>::T)
+k_phi_adj_rows(const float2 *__restrict__ inter, const float *__restrict__ inv_a, int N, float scale,
+               float *__restrict__ x_re, float2 *__restrict__ x_c, const float *__restrict__ z, int mode,
+               const float2 *__restrict__ tw) {
+  phi_adj_rows_body<LOGN>(inter, inv_a, N, scale, x_re, x_c, z, mode, tw, blockIdx.x);
+}
+
+template <int LOGN>
+__global__ void __launch_bounds__(RowCfg<LOGN>::T)
+k_bphi_adj_rows(const BProb *__restrict__ tab, const int32_t *__restrict__ plist, const float2 *__restrict__ inter,
+                const float *__restrict__ inv_a, float *__restrict__ x_re, const float *__restrict__ z, int mode,
+                const float2 *__restrict__ tw) {
+  const BProb P = tab[plist[blockIdx.y]];
+  phi_adj_rows_body<LOGN>(inter + P.inter_off, inv_a + P.inva_off, P.N, 1.0f / P.G, x_re + P.img_off, nullptr,
+                          z ? z + P.img_off : nullptr, mode, tw, blockIdx.x);
 }
 
 // ---- generic batched 2-D FFT (rows then columns) --------------------------------
@@ -389,18 +452,63 @@ wproj_status box_fft_impl(wproj_plan *p, const BoxBatch &bb, cudaStream_t s) {
 
 }  // namespace
 
+// ---- batches: one launch per pass for all problems of a size class ---------------
+
+template <int LOGN>
+wproj_status bphi_fwd_impl(int np, const int32_t *plist, const BProb *tab, const float *x, const float *inv_a,
+                           float2 *inter, float2 *Xt, const float2 *tw, cudaStream_t s) {
+  constexpr int G = 1 << LOGN;
+  const int N = G / 2;
+  {
+    using Cfg = RowCfg<LOGN>;
+    WPROJ_TRY(set_smem(k_bphi_fwd_rows<LOGN>, Cfg::SMEM));
+    k_bphi_fwd_rows<LOGN><<<dim3(ceil_div(N, Cfg::C), np), Cfg::T, Cfg::SMEM, s>>>(tab, plist, x, inv_a, inter, tw);
+    WPROJ_CHECK_LAUNCH("batch phi fwd rows");
+  }
+  {
+    using Cfg = ColCfg<LOGN>;
+    WPROJ_TRY(set_smem(k_bphi_fwd_cols<LOGN>, Cfg::SMEM));
+    k_bphi_fwd_cols<LOGN><<<dim3(ceil_div(G, Cfg::C), np), Cfg::T, Cfg::SMEM, s>>>(tab, plist, inter, Xt, tw);
+    WPROJ_CHECK_LAUNCH("batch phi fwd cols");
+  }
+  return WPROJ_OK;
+}
+
+template <int LOGN>
+wproj_status bphi_adj_impl(int np, const int32_t *plist, const BProb *tab, const float2 *Xt2, const float *inv_a,
+                           float2 *inter, float *x_re, const float *z, int mode, const float2 *tw, cudaStream_t s) {
+  constexpr int G = 1 << LOGN;
+  const int N = G / 2;
+  {
+    using Cfg = ColCfg<LOGN>;
+    WPROJ_TRY(set_smem(k_bphi_adj_cols<LOGN>, Cfg::SMEM));
+    k_bphi_adj_cols<LOGN><<<dim3(ceil_div(G, Cfg::C), np), Cfg::T, Cfg::SMEM, s>>>(tab, plist, Xt2, inter, tw);
+    WPROJ_CHECK_LAUNCH("batch phi adj cols");
+  }
+  {
+    using Cfg = RowCfg<LOGN>;
+    WPROJ_TRY(set_smem(k_bphi_adj_rows<LOGN>, Cfg::SMEM));
+    k_bphi_adj_rows<LOGN><<<dim3(ceil_div(N, Cfg::C), np), Cfg::T, Cfg::SMEM, s>>>(tab, plist, inter, inv_a, x_re,
+                                                                                 z, mode, tw);
+    WPROJ_CHECK_LAUNCH("batch phi adj rows");
+  }
+  return WPROJ_OK;
+}
+
 wproj_status phi_forward_fft_into(wproj_plan *p, const float *x, float2 *inter, float2 *Xt, cudaStream_t s) {
 #define CALL(L) phi_fwd_into_impl<L>(p, x, inter, Xt, s)
   WPROJ_LOGN_SWITCH(ilog2(p->g.G), CALL)
 #undef CALL
 }
 
-wproj_status init_twiddles(wproj_plan *p, cudaStream_t s) {
-  WPROJ_TRY(p->twiddle.alloc(sizeof(float2) * kTwiddleLen));
-  k_twiddles<<<kTwiddleLen / 256, 256, 0, s>>>(p->twiddle.as<float2>());
+wproj_status make_twiddles(DevBuf &tw, cudaStream_t s) {
+  WPROJ_TRY(tw.alloc(sizeof(float2) * kTwiddleLen));
+  k_twiddles<<<kTwiddleLen / 256, 256, 0, s>>>(tw.as<float2>());
   WPROJ_CHECK_LAUNCH("twiddles");
   return WPROJ_OK;
 }
+
+wproj_status init_twiddles(wproj_plan *p, cudaStream_t s) { return make_twiddles(p->twiddle, s); }
 
 wproj_status phi_forward_fft(wproj_plan *p, const float *x, const float2 *xc, float2 *Xt, cudaStream_t s) {
   ScopedTimer t(p, TC_FFT, s);
@@ -429,6 +537,21 @@ wproj_status fft2d_generic(const float2 *in, float2 *out, int n, int batch, int 
 wproj_status box_fft(wproj_plan *p, const BoxBatch &bb, cudaStream_t s) {
 #define CALL(L) box_fft_impl<L>(p, bb, s)
   WPROJ_LOGN_SWITCH(ilog2(bb.S), CALL)
+#undef CALL
+}
+
+wproj_status batch_phi_fwd(int logG, int np, const int32_t *plist, const BProb *tab, const float *x,
+                           const float *inv_a, float2 *inter, float2 *Xt, const float2 *tw, cudaStream_t s) {
+#define CALL(L) bphi_fwd_impl<L>(np, plist, tab, x, inv_a, inter, Xt, tw, s)
+  WPROJ_LOGN_SWITCH(logG, CALL)
+#undef CALL
+}
+
+wproj_status batch_phi_adj(int logG, int np, const int32_t *plist, const BProb *tab, const float2 *Xt2,
+                           const float *inv_a, float2 *inter, float *x_re, const float *z, int mode,
+                           const float2 *tw, cudaStream_t s) {
+#define CALL(L) bphi_adj_impl<L>(np, plist, tab, Xt2, inv_a, inter, x_re, z, mode, tw, s)
+  WPROJ_LOGN_SWITCH(logG, CALL)
 #undef CALL
 }
 

@@ -95,14 +95,24 @@ __device__ __forceinline__ void grid_acc(float2 *my, int q, float2 v, float2 yk,
   *cell = a;
 }
 
+// chunk_prob / tab (batches): the chunk's problem supplies logG, nT and the
+// offset of its grid, which the stored columns include
 template <int VDT, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
 k_grid(const int32_t *__restrict__ chunk_tile, const int64_t *__restrict__ chunk_lo,
        const int64_t *__restrict__ chunk_hi, const SegMeta *__restrict__ meta,
        const int32_t *__restrict__ col, const void *__restrict__ val, const float *__restrict__ row_scale,
-       const float2 *__restrict__ y, int logG, int TS, int nT, float2 *__restrict__ partial) {
+       const float2 *__restrict__ y, int logG, int TS, int nT, const int32_t *__restrict__ chunk_prob,
+       const BProb *__restrict__ tab, float2 *__restrict__ partial) {
   extern __shared__ float2 acc[];   // [WARPS][TS*TS]
   const int c = blockIdx.x;
+  int cbase = 0;
+  if (chunk_prob) {
+    const BProb &P = tab[chunk_prob[c]];
+    logG = P.logG;
+    nT = P.nT;
+    cbase = int(P.grid_off);
+  }
   const int tile = chunk_tile[c];
   const int tu = tile / nT, tv = tile % nT;
   const int cells = TS * TS;
@@ -127,8 +137,8 @@ k_grid(const int32_t *__restrict__ chunk_tile, const int64_t *__restrict__ chunk
     const int n = meta_cnt(cur);
     int i = lane;
     for (; i + 96 < n; i += 128) {
-      const int q0 = __ldg(col + off + i), q1 = __ldg(col + off + i + 32);
-      const int q2 = __ldg(col + off + i + 64), q3 = __ldg(col + off + i + 96);
+      const int q0 = __ldg(col + off + i) - cbase, q1 = __ldg(col + off + i + 32) - cbase;
+      const int q2 = __ldg(col + off + i + 64) - cbase, q3 = __ldg(col + off + i + 96) - cbase;
       const float2 v0 = load_val<VDT>(val, off + i), v1 = load_val<VDT>(val, off + i + 32);
       const float2 v2 = load_val<VDT>(val, off + i + 64), v3 = load_val<VDT>(val, off + i + 96);
       grid_acc(my, q0, v0, yk, logG, Gm, ou, ov, TS);
@@ -136,7 +146,8 @@ k_grid(const int32_t *__restrict__ chunk_tile, const int64_t *__restrict__ chunk
       grid_acc(my, q2, v2, yk, logG, Gm, ou, ov, TS);
       grid_acc(my, q3, v3, yk, logG, Gm, ou, ov, TS);
     }
-    for (; i < n; i += 32) grid_acc(my, __ldg(col + off + i), load_val<VDT>(val, off + i), yk, logG, Gm, ou, ov, TS);
+    for (; i < n; i += 32)
+      grid_acc(my, __ldg(col + off + i) - cbase, load_val<VDT>(val, off + i), yk, logG, Gm, ou, ov, TS);
     if (more) cur = nxt;
   }
   __syncthreads();
@@ -149,12 +160,21 @@ k_grid(const int32_t *__restrict__ chunk_tile, const int64_t *__restrict__ chunk
   }
 }
 
+// tile_prob / tab (batches): blockIdx.x is a tile of the whole batch
 __global__ void k_grid_reduce(const int32_t *__restrict__ tile_chunk_ptr, const float2 *__restrict__ partial,
-                              int G, int TS, int nT, float2 *__restrict__ Xt2) {
-  const int tile = blockIdx.x;
+                              int G, int TS, int nT, const int32_t *__restrict__ tile_prob,
+                              const BProb *__restrict__ tab, float2 *__restrict__ Xt2) {
+  int tile = blockIdx.x;
+  const int c0 = tile_chunk_ptr[tile], c1 = tile_chunk_ptr[tile + 1];
+  if (tile_prob) {
+    const BProb &P = tab[tile_prob[tile]];
+    G = P.G;
+    nT = P.nT;
+    tile -= int(P.tile_off);
+    Xt2 += P.grid_off;
+  }
   const int tu = tile / nT, tv = tile % nT;
   const int cells = TS * TS;
-  const int c0 = tile_chunk_ptr[tile], c1 = tile_chunk_ptr[tile + 1];
   for (int i = threadIdx.x; i < cells; i += blockDim.x) {
     float2 s = make_float2(0.f, 0.f);
     for (int c = c0; c < c1; ++c) s = cadd(s, partial[int64_t(c) * cells + i]);
@@ -222,8 +242,8 @@ wproj_status grid(wproj_plan *p, const float2 *y, float2 *Xt2, cudaStream_t s) {
     WPROJ_CUDA(cudaFuncSetAttribute(k_grid<VDT, kGridWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
     k_grid<VDT, kGridWarps><<<(unsigned)p->n_chunks, kGridWarps * 32, smem, s>>>(                           \
         p->chunk_tile.as<int32_t>(), p->chunk_lo.as<int64_t>(), p->chunk_hi.as<int64_t>(),                  \
-        p->seg_meta.as<SegMeta>(), p->col.as<int32_t>(), p->val.ptr, rs, y, logG, g.tile, g.nT,             \
-        p->grid_partial.as<float2>());                                                                      \
+        p->seg_meta.as<SegMeta>(), p->col.as<int32_t>(), p->val.ptr, rs, y, logG, g.tile, g.nT, nullptr,    \
+        nullptr, p->grid_partial.as<float2>());                                                             \
   } while (0)
     if (p->fmt == WPROJ_INDEX_TILE_MASK) {
       WPROJ_TRY(grid_stream(p, y, s));
@@ -239,7 +259,7 @@ wproj_status grid(wproj_plan *p, const float2 *y, float2 *Xt2, cudaStream_t s) {
   }
   ScopedTimer t(p, TC_REDUCE, s);
   k_grid_reduce<<<g.nT * g.nT, 256, 0, s>>>(p->tile_chunk_ptr.as<int32_t>(), p->grid_partial.as<float2>(), g.G, g.tile,
-                                             g.nT, Xt2);
+                                             g.nT, nullptr, nullptr, Xt2);
   WPROJ_CHECK_LAUNCH("grid reduce");
   return WPROJ_OK;
 }
@@ -259,6 +279,31 @@ wproj_status csr_rows(const wproj_plan *p, int64_t k0, int64_t k1, int32_t *col_
   if (val_out)
     WPROJ_CUDA(cudaMemcpyAsync(val_out, static_cast<const unsigned char *>(p->val.ptr) + vb * r[0], vb * n,
                                cudaMemcpyDeviceToDevice, s));
+  return WPROJ_OK;
+}
+
+// ---- batches: the column-format kernels over a batch's concatenated arrays ------
+
+wproj_status batch_degrid(const BatchOps &b, const float2 *Xt, float2 *partial, float2 *y, cudaStream_t s) {
+  const int blocks = (int)std::min<int64_t>(ceil_div(b.n_pieces * 32, 256), 152 * 16);
+  k_degrid<WPROJ_VAL_F32><<<std::max(blocks, 1), 256, 0, s>>>(b.n_pieces, b.piece_row, b.piece_lo, b.piece_len,
+                                                              b.col, b.val, Xt, partial);
+  WPROJ_CHECK_LAUNCH("batch degrid");
+  k_degrid_reduce<<<ceil_div(b.m, 256), 256, 0, s>>>(b.m, b.row_piece_ptr, partial, nullptr, y);
+  WPROJ_CHECK_LAUNCH("batch degrid reduce");
+  return WPROJ_OK;
+}
+
+wproj_status batch_grid(const BatchOps &b, const float2 *y, float2 *partial, float2 *Xt2, cudaStream_t s) {
+  const size_t smem = sizeof(float2) * kGridWarps * kTile * kTile;
+  WPROJ_CUDA(cudaFuncSetAttribute(k_grid<WPROJ_VAL_F32, kGridWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+  k_grid<WPROJ_VAL_F32, kGridWarps><<<(unsigned)b.n_chunks, kGridWarps * 32, smem, s>>>(
+      b.chunk_tile, b.chunk_lo, b.chunk_hi, b.meta, b.col, b.val, nullptr, y, 0, kTile, 0, b.chunk_prob, b.tab,
+      partial);
+  WPROJ_CHECK_LAUNCH("batch grid");
+  k_grid_reduce<<<(unsigned)b.n_tiles, 256, 0, s>>>(b.tile_chunk_ptr, partial, 0, kTile, 0, b.tile_prob, b.tab, Xt2);
+  WPROJ_CHECK_LAUNCH("batch grid reduce");
   return WPROJ_OK;
 }
 

@@ -40,6 +40,32 @@ __host__ __device__ __forceinline__ long long meta_off(const SegMeta &m) {
 }
 __host__ __device__ __forceinline__ int meta_cnt(const SegMeta &m) { return (int)(m.off_cnt >> 40); }
 
+// One problem of a batch (wproj_batch): its geometry and where its arrays sit in
+// the batch's concatenated buffers.
+struct BProb {
+  int N, G, logG, nT;
+  int64_t m;
+  int64_t img_off;     // images: N*N floats
+  int64_t vis_off;     // visibilities
+  int64_t grid_off;    // grids: G*G complex; also added to the stored columns
+  int64_t inter_off;   // FFT intermediates: N*G complex
+  int64_t inva_off;    // 1/a(l) tables: N floats
+  int64_t tile_off;    // first of its nT*nT grid tiles in the batch's tile order
+};
+
+// The column-format operator arrays of a batch (concatenated over problems).
+struct BatchOps {
+  int64_t m = 0, n_pieces = 0, n_chunks = 0, n_tiles = 0;
+  const int32_t *col = nullptr;          // columns + the problem's grid_off
+  const void *val = nullptr;             // complex64
+  const int32_t *piece_row = nullptr, *piece_len = nullptr, *row_piece_ptr = nullptr;
+  const int64_t *piece_lo = nullptr;
+  const int32_t *chunk_tile = nullptr, *chunk_prob = nullptr, *tile_chunk_ptr = nullptr, *tile_prob = nullptr;
+  const int64_t *chunk_lo = nullptr, *chunk_hi = nullptr;
+  const SegMeta *meta = nullptr;         // tile order, entry offsets and rows of the batch
+  const BProb *tab = nullptr;
+};
+
 // Timing accumulator for one class of kernels.
 enum TimerClass { TC_FFT = 0, TC_DEGRID, TC_GRID, TC_REDUCE, TC_SOLVER, TC_COUNT };
 
@@ -144,6 +170,7 @@ struct ScopedTimer {
 
 // fft.cu
 wproj_status init_twiddles(wproj_plan *p, cudaStream_t s);
+wproj_status make_twiddles(DevBuf &tw, cudaStream_t s);
 wproj_status phi_forward_fft(wproj_plan *p, const float *x, const float2 *xc, float2 *Xt, cudaStream_t s);
 // mode 0: x_re = Re(...), x_cplx optional; mode 1: x_re = z - Re(...)
 wproj_status phi_adjoint_fft(wproj_plan *p, const float2 *Xt2, float *x_re, float2 *x_cplx,
@@ -155,6 +182,12 @@ struct BoxBatch;
 wproj_status box_fft(wproj_plan *p, const BoxBatch &bb, cudaStream_t s);
 
 wproj_status phi_forward_fft_into(wproj_plan *p, const float *x, float2 *inter, float2 *Xt, cudaStream_t s);
+// batches: F Z A and A Z^H F^H for the np problems plist (device) of one grid size 2^logG
+wproj_status batch_phi_fwd(int logG, int np, const int32_t *plist, const BProb *tab, const float *x,
+                           const float *inv_a, float2 *inter, float2 *Xt, const float2 *tw, cudaStream_t s);
+wproj_status batch_phi_adj(int logG, int np, const int32_t *plist, const BProb *tab, const float2 *Xt2,
+                           const float *inv_a, float2 *inter, float *x_re, const float *z, int mode,
+                           const float2 *tw, cudaStream_t s);
 
 // ops.cu
 wproj_status degrid(wproj_plan *p, const float2 *Xt, float2 *y, cudaStream_t s);
@@ -162,6 +195,10 @@ wproj_status degrid_into(wproj_plan *p, const float2 *Xt, float2 *partial, float
 wproj_status csr_rows(const wproj_plan *p, int64_t k0, int64_t k1, int32_t *col_out, void *val_out,
                       cudaStream_t s);
 int64_t degrid_partials(const wproj_plan *p);   // partial sums degridding needs
+
+// batches (column format)
+wproj_status batch_degrid(const BatchOps &b, const float2 *Xt, float2 *partial, float2 *y, cudaStream_t s);
+wproj_status batch_grid(const BatchOps &b, const float2 *y, float2 *partial, float2 *Xt2, cudaStream_t s);
 
 // tiles.cu (tile-stream records, TILE_MASK format)
 int64_t degrid_stream_partials(const wproj_plan *p);
@@ -174,6 +211,15 @@ wproj_status grid(wproj_plan *p, const float2 *y, float2 *Xt2, cudaStream_t s);
 wproj_status apply_phi(wproj_plan *p, const float *x, const float2 *xc, float2 *y, cudaStream_t s);
 wproj_status apply_phi_adj(wproj_plan *p, const float2 *y, float *x_re, float2 *x_cplx,
                            const float *z, int mode, cudaStream_t s);
+
+// build.cu: work units shared by plans and batches
+// row pieces of <= piece entries (m rows, row_ptr[m+1])
+wproj_status make_row_pieces(int64_t m, const int64_t *row_ptr, int64_t piece, DevBuf &piece_row, DevBuf &piece_lo,
+                             DevBuf &piece_len, DevBuf &row_piece_ptr, int64_t *n_pieces, cudaStream_t s);
+// chunks of about `chunk` entries of each tile's segments [tptr[t], tptr[t+1]) (cum = entry prefix)
+wproj_status make_tile_chunks(int n_tiles, const int64_t *tptr, const int64_t *cum, int64_t n_seg, int64_t nnz,
+                              int64_t chunk, DevBuf &chunk_tile, DevBuf &chunk_lo, DevBuf &chunk_hi,
+                              DevBuf &tile_chunk_ptr, int64_t *n_chunks, cudaStream_t s);
 
 // scan.cu
 wproj_status exclusive_scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, cudaStream_t s);

@@ -22,25 +22,6 @@ namespace {
 constexpr int kRedThreads = 256;
 constexpr int kRedBlocks = 304;   // 2 x 152 SMs
 
-__device__ __forceinline__ double warp_sum_d(double v) {
-  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-__device__ __forceinline__ double block_sum_d(double v) {
-  __shared__ double red[kRedThreads / 32];
-  v = warp_sum_d(v);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  double t = 0;
-  if (threadIdx.x < 32) {
-    t = (threadIdx.x < kRedThreads / 32) ? red[threadIdx.x] : 0.0;
-    t = warp_sum_d(t);
-  }
-  __syncthreads();
-  return t;   // valid in thread 0
-}
-
 // d = u/mu + r - y (written over r); partial sums of |d|^2
 __global__ void __launch_bounds__(kRedThreads)
 k_dual_residual(int64_t m, const float2 *__restrict__ u, float2 *__restrict__ r,
@@ -52,7 +33,7 @@ k_dual_residual(int64_t m, const float2 *__restrict__ u, float2 *__restrict__ r,
     r[i] = d;
     acc += double(d.x) * d.x + double(d.y) * d.y;
   }
-  const double t = block_sum_d(acc);
+  const double t = block_sum_d<kRedThreads>(acc);
   if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
@@ -119,7 +100,7 @@ k_sum_part(int64_t n, const float *__restrict__ x, double *__restrict__ part) {
     const double v = x[i];
     acc += ABS ? fabs(v) : v * v;
   }
-  const double t = block_sum_d(acc);
+  const double t = block_sum_d<kRedThreads>(acc);
   if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
@@ -130,7 +111,7 @@ k_resid_part(int64_t m, const float2 *__restrict__ a, const float2 *__restrict__
     const double dx = double(a[i].x) - b[i].x, dy = double(a[i].y) - b[i].y;
     acc += dx * dx + dy * dy;
   }
-  const double t = block_sum_d(acc);
+  const double t = block_sum_d<kRedThreads>(acc);
   if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 

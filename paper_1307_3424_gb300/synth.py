@@ -183,3 +183,49 @@ def random_uvw(rng: np.random.Generator, M: int, N: int, L: float,
     uv = uv_points(rng, M, B, N, "uniform")
     w = w_from_wd(rng.uniform(0.0, wd_max, M), N, L)
     return np.ascontiguousarray(np.concatenate([uv, w[:, None]], axis=1))
+
+
+# The batched form: many independent problems of uneven size.  Image sides are
+# drawn log-uniformly from the powers of two 64 .. 512 (the FFTs are radix 2/4),
+# M = f N^2 with f ~ U[0.1, 1], a per-problem w_c,max ~ U[0, 2] cells with
+# w_c ~ U[0, w_c,max] per visibility (chirp half-band h = 2 w_c), uniform-disk
+# (u, v), blob skies with 20 (N/64)^2 blobs, box rule S(w), e = 0.99.
+@dataclass
+class BatchWorkload:
+    name: str
+    n_problems: int
+    sides: tuple = (64, 128, 256, 512)
+    mfrac: tuple = (0.1, 1.0)
+    wc_max: float = 2.0
+    e: float = 0.99
+    dr_iters: int = 200
+    inner_iters: int = 10
+    snr_in_db: float = 30.0
+
+
+BATCHED = BatchWorkload("batch256_n64-512", n_problems=256)
+
+
+def make_batch(bw: BatchWorkload, seed: int = 0, n_problems: int | None = None,
+               max_side: int | None = None) -> list[Problem]:
+    """Problems of a batch; problem i is drawn from PCG64(seed * 1_000_003 + i)
+    in the order side -> M -> w_c,max -> sky -> uv -> w (noise: draw_noise)."""
+    n_problems = bw.n_problems if n_problems is None else n_problems
+    sides = [s for s in bw.sides if max_side is None or s <= max_side]
+    L = fov_L()
+    out = []
+    for i in range(n_problems):
+        rng = np.random.Generator(np.random.PCG64(seed * 1_000_003 + i))
+        N = int(sides[rng.integers(0, len(sides))])
+        M = max(1, int(round(rng.uniform(*bw.mfrac) * N * N)))
+        wcm = rng.uniform(0.0, bw.wc_max)
+        wl = Workload(f"{bw.name}[{i}]", N=N, n_blobs=max(1, 20 * (N // 64) ** 2), M=M, uv="uniform",
+                      wd_max=wcm, e=bw.e, dr_iters=bw.dr_iters, inner_iters=bw.inner_iters,
+                      snr_in_db=bw.snr_in_db, w_unit="cells", box="rule")
+        x = blob_sky(rng, N, wl.n_blobs)
+        uv = uv_points(rng, M, band_limit(N, L), N, "uniform")
+        wc = rng.uniform(0.0, wcm, M)
+        w = 2.0 * wc / (L * L)
+        uvw = np.ascontiguousarray(np.concatenate([uv, w[:, None]], axis=1))
+        out.append(Problem(wl, L, x, uvw, wc, rng))
+    return out

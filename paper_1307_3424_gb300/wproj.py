@@ -28,6 +28,9 @@ EXPORTED = [
     "wproj_fft2d", "wproj_set_timing", "wproj_get_stats", "wproj_reset_stats",
     "wproj_dr_defaults", "wproj_last_error", "wproj_version", "wproj_dr_state_get",
     "wproj_dr_state_set", "wproj_phi_noalloc", "wproj_csr_rows",
+    "wproj_batch_create", "wproj_batch_destroy", "wproj_batch_build", "wproj_batch_tune",
+    "wproj_batch_set_schedule", "wproj_batch_phi", "wproj_batch_phi_adj", "wproj_batch_solve_bpdn",
+    "wproj_batch_get_info",
 ]
 
 
@@ -62,6 +65,18 @@ class SolveInfo(ctypes.Structure):
     _fields_ = [("iters_done", ctypes.c_int32), ("phi_norm2", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("final_resid", ctypes.c_double),
                 ("final_l1", ctypes.c_double)]
+
+
+class BatchSchedule(ctypes.Structure):
+    _fields_ = [("piece", ctypes.c_int64), ("chunk", ctypes.c_int64), ("degrid_ms", ctypes.c_double),
+                ("grid_ms", ctypes.c_double)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("n_problems", ctypes.c_int32), ("m", ctypes.c_int64), ("pixels", ctypes.c_int64),
+                ("nnz", ctypes.c_int64), ("n_pieces", ctypes.c_int64), ("n_chunks", ctypes.c_int64),
+                ("piece", ctypes.c_int64), ("chunk", ctypes.c_int64), ("launches", ctypes.c_int64),
+                ("iter_launches", ctypes.c_int64)]
 
 
 class Stats(ctypes.Structure):
@@ -111,6 +126,15 @@ def lib() -> ctypes.CDLL:
         "wproj_reset_stats": [vp],
         "wproj_dr_state_get": [vp, vp, vp, P(dbl), P(dbl), vp],
         "wproj_dr_state_set": [vp, vp, vp, dbl, dbl, vp],
+        "wproj_batch_create": [P(vp), i32, P(GridDesc)],
+        "wproj_batch_destroy": [vp],
+        "wproj_batch_build": [vp, vp, P(i64), dbl, vp],
+        "wproj_batch_tune": [vp, P(BatchSchedule), vp],
+        "wproj_batch_set_schedule": [vp, i64, i64, vp],
+        "wproj_batch_phi": [vp, vp, vp, vp],
+        "wproj_batch_phi_adj": [vp, vp, vp, vp],
+        "wproj_batch_solve_bpdn": [vp, vp, P(dbl), P(DRParams), vp, vp],
+        "wproj_batch_get_info": [vp, P(BatchInfo)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -361,3 +385,106 @@ def fft2d(x: torch.Tensor, inverse: bool = False, out: torch.Tensor | None = Non
         out = torch.empty_like(x)
     _check(lib().wproj_fft2d(_ptr(x), _ptr(out), n, batch, 1 if inverse else 0, _stream(stream)))
     return out
+
+
+class Batch:
+    """Many independent problems (image sides ns, shared field of view) whose
+    operators and Douglas-Rachford iterations run as shared launches
+    (include/wproj.h, wproj_batch_*).  Images, visibilities and uvw are
+    concatenated in problem order; `split_images` / `split_vis` cut them apart."""
+
+    def __init__(self, ns, fov: float, kb_support: int = 4, chirp: str = "exact", extension: str = "full",
+                 box="rule"):
+        self._h = ctypes.c_void_p()
+        self.ns = [int(n) for n in ns]
+        descs = (GridDesc * len(self.ns))()
+        for i, n in enumerate(self.ns):
+            box_i = 2 * n if box in ("G", None) else (0 if box == "rule" else int(box))
+            descs[i] = GridDesc(n, kb_support, float(fov), CHIRP[chirp], EXTENSION[extension], box_i,
+                                VALUE_DTYPE["f32"], INDEX_FORMAT["columns"])
+        self.img_off = [0]
+        for n in self.ns:
+            self.img_off.append(self.img_off[-1] + n * n)
+        self.ms, self.vis_off = [], [0]
+        _check(lib().wproj_batch_create(ctypes.byref(self._h), len(self.ns), descs))
+
+    def close(self):
+        if self._h:
+            lib().wproj_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def pixels(self) -> int:
+        return self.img_off[-1]
+
+    @property
+    def m(self) -> int:
+        return self.vis_off[-1]
+
+    def build_kernels(self, uvw: torch.Tensor, ms, e: float, stream=None):
+        """uvw: (sum ms, 3) float64 on the device, problems in order."""
+        self.ms = [int(m) for m in ms]
+        self.vis_off = [0]
+        for m in self.ms:
+            self.vis_off.append(self.vis_off[-1] + m)
+        if uvw.dtype != torch.float64 or tuple(uvw.shape) != (self.m, 3):
+            raise WprojError(ERR_INVALID_ARG, f"uvw must be a ({self.m}, 3) float64 tensor")
+        arr = (ctypes.c_int64 * len(self.ms))(*self.ms)
+        _check(lib().wproj_batch_build(self._h, _ptr(uvw.contiguous()), arr, float(e), _stream(stream)))
+
+    def tune(self, stream=None) -> dict:
+        out = BatchSchedule()
+        _check(lib().wproj_batch_tune(self._h, ctypes.byref(out), _stream(stream)))
+        return {f: getattr(out, f) for f, _ in out._fields_}
+
+    def set_schedule(self, piece: int, chunk: int, stream=None):
+        _check(lib().wproj_batch_set_schedule(self._h, int(piece), int(chunk), _stream(stream)))
+
+    def info(self) -> dict:
+        out = BatchInfo()
+        _check(lib().wproj_batch_get_info(self._h, ctypes.byref(out)))
+        return {f: getattr(out, f) for f, _ in out._fields_}
+
+    def phi(self, x: torch.Tensor, y: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        if x.dtype != torch.float32 or x.numel() != self.pixels:
+            raise WprojError(ERR_INVALID_ARG, f"x must hold {self.pixels} float32 pixels")
+        if y is None:
+            y = torch.empty(self.m, dtype=torch.complex64, device=x.device)
+        _check(lib().wproj_batch_phi(self._h, _ptr(x), _ptr(y), _stream(stream)))
+        return y
+
+    def phi_adj(self, y: torch.Tensor, x: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        if y.dtype != torch.complex64 or y.numel() != self.m:
+            raise WprojError(ERR_INVALID_ARG, f"y must hold {self.m} complex64 visibilities")
+        if x is None:
+            x = torch.empty(self.pixels, dtype=torch.float32, device=y.device)
+        _check(lib().wproj_batch_phi_adj(self._h, _ptr(y), _ptr(x), _stream(stream)))
+        return x
+
+    def solve_bpdn(self, y: torch.Tensor, eps, iters: int = 50, inner_iters: int = 10, gamma_frac: float = 1e-2,
+                   lam: float = 1.0, power_iters: int = 100, x_out: torch.Tensor | None = None,
+                   resume: bool = False, stream=None) -> torch.Tensor:
+        if y.dtype != torch.complex64 or y.numel() != self.m:
+            raise WprojError(ERR_INVALID_ARG, f"y must hold {self.m} complex64 visibilities")
+        eps = [float(v) for v in eps]
+        if len(eps) != len(self.ns):
+            raise WprojError(ERR_INVALID_ARG, "one eps per problem")
+        prm = DRParams(iters, inner_iters, gamma_frac, lam, 0.0, power_iters, 1 if resume else 0)
+        if x_out is None:
+            x_out = torch.empty(self.pixels, dtype=torch.float32, device=y.device)
+        arr = (ctypes.c_double * len(eps))(*eps)
+        _check(lib().wproj_batch_solve_bpdn(self._h, _ptr(y), arr, ctypes.byref(prm), _ptr(x_out),
+                                            _stream(stream)))
+        return x_out
+
+    def split_images(self, x: torch.Tensor):
+        return [x[a:b].view(n, n) for a, b, n in zip(self.img_off[:-1], self.img_off[1:], self.ns)]
+
+    def split_vis(self, y: torch.Tensor):
+        return [y[a:b] for a, b in zip(self.vis_off[:-1], self.vis_off[1:])]
