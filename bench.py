@@ -52,7 +52,9 @@ def parse():
     ap.add_argument("--value-dtype", default="f32", choices=["f32", "bf16", "f16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-rows", type=int, default=64)
-    ap.add_argument("--workload", default="paper", choices=["paper", "precision"])
+    ap.add_argument("--workload", default="paper", choices=["paper", "precision", "batched"])
+    ap.add_argument("--batch-problems", type=int, default=None, help="problems of the batched workload")
+    ap.add_argument("--no-plain", action="store_true", help="batched workload: skip the one-by-one comparison")
     ap.add_argument("--index-format", default="auto", choices=["auto", "columns", "mask"])
     ap.add_argument("--n", type=int, default=None, help="image side of a smaller profiling case")
     ap.add_argument("--m", type=int, default=None, help="visibilities of a smaller profiling case")
@@ -400,10 +402,148 @@ def run_ours(args):
     return out, kst
 
 
+def run_batched(args):
+    """The batched workload (256 problems, N in {64 .. 512}, M = f N^2): one step
+    is one Douglas-Rachford iteration of every problem, replayed from the
+    captured graph; the same problems run one by one through single plans are
+    timed beside it (the plain GPU form)."""
+    import torch
+    from oracle import wproj_oracle as O
+    from paper_1307_3424_gb300 import wproj
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    bw = synth.BATCHED
+    probs = synth.make_batch(bw, seed=0, n_problems=args.batch_problems)
+    ns = [p.wl.N for p in probs]
+    ms = [p.uvw.shape[0] for p in probs]
+    L = probs[0].L
+    noise, sig = [], []
+    for p in probs:
+        nz, s_n = synth.draw_noise(p)
+        noise.append(nz)
+        sig.append(s_n)
+    eps = [O.epsilon_chi2(s_n, m) for s_n, m in zip(sig, ms)]
+    uvw = torch.from_numpy(np.concatenate([p.uvw for p in probs])).to(dev)
+    b = wproj.Batch(ns, L, box="rule")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.build_kernels(uvw, ms, bw.e)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    sched = b.tune()
+    info = b.info()
+    x_cat = torch.from_numpy(np.concatenate([p.x.ravel() for p in probs]).astype(np.float32)).to(dev)
+    y = b.phi(x_cat) + torch.from_numpy(np.concatenate(noise).astype(np.complex64)).to(dev)
+    x_out = torch.empty(b.pixels, dtype=torch.float32, device=dev)
+    b.solve_bpdn(y, eps, iters=1, inner_iters=INNER, x_out=x_out)       # power iterations, graph capture
+    info = b.info()
+    for _ in range(args.warmup):
+        b.solve_bpdn(y, eps, iters=1, inner_iters=INNER, x_out=x_out, resume=True)
+    torch.cuda.synchronize()
+    l0 = b.info()["launches"]
+    clocks = ClockSampler(0)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        b.solve_bpdn(y, eps, iters=1, inner_iters=INNER, x_out=x_out, resume=True)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t_ms = ev0.elapsed_time(ev1)
+    launches = b.info()["launches"] - l0
+    snr_batch = [O.snr_db(p.x, xi.cpu().numpy().astype(np.float64)) for p, xi in zip(probs, b.split_images(x_out))]
+    # end to end: visibilities from pinned host memory, images back, every step
+    y_host = y.cpu().pin_memory()
+    x_host = torch.empty(b.pixels, dtype=torch.float32).pin_memory()
+    y2 = torch.empty_like(y)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        y2.copy_(y_host, non_blocking=True)
+        b.solve_bpdn(y2, eps, iters=1, inner_iters=INNER, x_out=x_out, resume=True)
+        x_host.copy_(x_out, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_e2e = e0.elapsed_time(e1)
+
+    plain = None
+    if not args.no_plain:
+        # the same problems one by one through single plans, same state
+        plans = []
+        for p, m_p, eps_p, y_p in zip(probs, ms, eps, b.split_vis(y)):
+            pl = wproj.Plan(p.wl.N, L, box="rule", index_format="columns")
+            pl.build_kernels(torch.from_numpy(p.uvw).to(dev), bw.e)
+            y_p = y_p.contiguous()
+            _, inf = pl.solve_bpdn(y_p, eps_p, iters=1 + args.warmup + args.steps, inner_iters=INNER)
+            xo = torch.empty((p.wl.N, p.wl.N), dtype=torch.float32, device=dev)
+            plans.append((pl, y_p, eps_p, inf.phi_norm2, xo))
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for _ in range(args.steps):
+            for pl, y_p, eps_p, n2, xo in plans:
+                pl.solve_bpdn(y_p, eps_p, iters=1, inner_iters=INNER, phi_norm2=n2, resume=True, sync=False,
+                              x_out=xo)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        t_plain = p0.elapsed_time(p1)
+        snr_plain = []
+        for (pl, y_p, eps_p, n2, xo), p in zip(plans, probs):
+            snr_plain.append(O.snr_db(p.x, xo.cpu().numpy().astype(np.float64)))
+            pl.close()
+        # both arms have now run 1 + warmup + 2 steps iterations (the batch: timed + e2e)
+        plain = {"value": PAIRS_PER_STEP * args.steps / (t_plain * 1e-3), "unit": "batch pairs/s",
+                 "ms_per_step": t_plain / args.steps, "form": "one plan per problem, solved one after another",
+                 "speedup_of_batch": t_plain / t_ms}
+        snr_b2 = [O.snr_db(p.x, xi.cpu().numpy().astype(np.float64)) for p, xi in zip(probs, b.split_images(x_out))]
+        plain["max_abs_snr_diff_db"] = float(max(abs(a - c) for a, c in zip(snr_b2, snr_plain)))
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    grid_cells = sum(4 * n * n for n in ns)
+    alg = info["nnz"] * 8 + info["m"] * 8 + grid_cells * 8
+    dom = "grid" if sched["grid_ms"] >= sched["degrid_ms"] else "degrid"
+    ms_dom = max(sched["grid_ms"], sched["degrid_ms"])
+    value = PAIRS_PER_STEP * args.steps / (t_ms * 1e-3)
+    line = {
+        "metric": "batch_phi_phiH_pairs_per_s", "value": value, "unit": "batch pairs/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": bw.name, "problems": len(ns), "sides": {str(n): ns.count(n) for n in sorted(set(ns))},
+                   "M_total": info["m"], "pixels_total": info["pixels"], "nnz": info["nnz"], "e": bw.e,
+                   "w_c_max": f"U[0, {bw.wc_max}] per problem", "box": "rule S(w)", "dr_inner_iters": INNER,
+                   "pairs_per_step": PAIRS_PER_STEP, "index_format": "columns",
+                   "schedule": {"piece": sched["piece"], "chunk": sched["chunk"]},
+                   "l2": "inputs larger than L2 (G exceeds L2 many times)", "parallelism": "one GPU"},
+        "problem_pairs_per_s": value * len(ns),
+        "e2e": {"value": PAIRS_PER_STEP * args.steps / (t_e2e * 1e-3), "unit": "batch pairs/s",
+                "h2d_bytes_per_step": info["m"] * 8, "d2h_bytes_per_step": info["pixels"] * 4},
+        "gpu_launches": int(launches),
+        "launches_per_step": info["iter_launches"],
+        "roofline": {"kernel": f"k_{dom} (batch, column format)", "bound": "hbm",
+                     "achieved": alg / (ms_dom * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": alg / (ms_dom * 1e-3) / 1e9 / hbm_peak, "traffic": None,
+                     "peak_source": "measured (copy bandwidth)", "algorithmic_bytes_per_launch": alg,
+                     "degrid_ms": sched["degrid_ms"], "grid_ms": sched["grid_ms"],
+                     "timing": "autotuner's CUDA-event timing of the chosen schedules"},
+        "plain_gpu": plain,
+        "snr_db_mean": float(np.mean(snr_batch)),
+        "build": {"ms": build_s * 1e3, "w_kernels_per_s": info["m"] / build_s, "nnz": info["nnz"]},
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
     res = run_ours(args)
     out, kst = res
     if out is not None:

@@ -40,6 +40,8 @@ struct wproj_batch {
   // G of all problems
   bool built = false;
   wproj::DevBuf row_ptr, col, val, meta, tptr, cum, tile_prob;
+  bool has_cells = false;   // cell-major copy for the gridding (every problem has one)
+  wproj::DevBuf tile_ent, cell_ent, cell_val;
   // schedule
   int64_t piece = 0, chunk = 0, n_pieces = 0, n_chunks = 0;
   wproj::DevBuf piece_row, piece_lo, piece_len, row_piece_ptr;
@@ -248,6 +250,11 @@ BatchOps ops_of(const wproj_batch *b) {
   o.chunk_hi = b->chunk_hi.as<int64_t>();
   o.meta = b->meta.as<SegMeta>();
   o.tab = b->tab.as<BProb>();
+  if (b->has_cells) {
+    o.tile_ent = b->tile_ent.as<int64_t>();
+    o.cell_ent = b->cell_ent.as<uint32_t>();
+    o.cell_val = b->cell_val.ptr;
+  }
   return o;
 }
 
@@ -454,6 +461,17 @@ wproj_status batch_build_impl(wproj_batch *b, const double *uvw, const int64_t *
   WPROJ_TRY(b->tptr.alloc(sizeof(int64_t) * (tiles + 1)));
   WPROJ_TRY(b->tile_prob.alloc(sizeof(int32_t) * tiles));
   WPROJ_TRY(b->inv_a.alloc(sizeof(float) * inva));
+  b->has_cells = true;
+  for (auto *pl : plans) b->has_cells = b->has_cells && pl->has_cells;
+  if (b->has_cells) {
+    WPROJ_TRY(b->tile_ent.alloc(sizeof(int64_t) * (tiles + 1)));
+    WPROJ_TRY(b->cell_ent.alloc(sizeof(uint32_t) * std::max<int64_t>(1, nnz)));
+    WPROJ_TRY(b->cell_val.alloc(sizeof(float2) * std::max<int64_t>(1, nnz)));
+  } else {
+    b->tile_ent.release();
+    b->cell_ent.release();
+    b->cell_val.release();
+  }
   int64_t ent = 0, sg = 0;
   for (int p = 0; p < np; ++p) {
     wproj_plan *pl = plans[p];
@@ -476,11 +494,24 @@ wproj_status batch_build_impl(wproj_batch *b, const double *uvw, const int64_t *
     WPROJ_CHECK_LAUNCH("batch concatenation");
     WPROJ_CUDA(cudaMemcpyAsync(b->inv_a.as<float>() + P.inva_off, pl->inv_a.ptr, sizeof(float) * P.N,
                                cudaMemcpyDeviceToDevice, s));
+    if (b->has_cells) {   // rows stay local to the problem; tiles and entries shift
+      k_add_i64<<<ceil_div(nt, 256), 256, 0, s>>>(nt, pl->tile_ent.as<int64_t>(), ent,
+                                                  b->tile_ent.as<int64_t>() + P.tile_off);
+      if (pl->nnz > 0) {
+        WPROJ_CUDA(cudaMemcpyAsync(b->cell_ent.as<uint32_t>() + ent, pl->cell_ent.ptr, sizeof(uint32_t) * pl->nnz,
+                                   cudaMemcpyDeviceToDevice, s));
+        WPROJ_CUDA(cudaMemcpyAsync(b->cell_val.as<float2>() + ent, pl->cell_val.ptr, sizeof(float2) * pl->nnz,
+                                   cudaMemcpyDeviceToDevice, s));
+      }
+      WPROJ_CHECK_LAUNCH("batch cell concatenation");
+    }
     ent += pl->nnz;
     sg += pl->n_seg;
   }
   WPROJ_CUDA(cudaMemcpyAsync(b->row_ptr.as<int64_t>() + vis, &nnz, sizeof(int64_t), cudaMemcpyHostToDevice, s));
   WPROJ_CUDA(cudaMemcpyAsync(b->tptr.as<int64_t>() + tiles, &nseg, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  if (b->has_cells)
+    WPROJ_CUDA(cudaMemcpyAsync(b->tile_ent.as<int64_t>() + tiles, &nnz, sizeof(int64_t), cudaMemcpyHostToDevice, s));
   // entry prefix over the tile-ordered segments (chunk balancing)
   {
     DevBuf cnt;

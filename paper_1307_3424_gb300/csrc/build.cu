@@ -1047,6 +1047,15 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
     }
     WPROJ_TRY(make_tile_chunks(n_tiles, tptr.as<int64_t>(), cum.as<int64_t>(), n_seg, p->nnz, chunk, p->chunk_tile,
                                p->chunk_lo, p->chunk_hi, p->tile_chunk_ptr, &p->n_chunks, s));
+    // column format: a cell-major copy for the gridding (packed rows need m <= 2^22)
+    p->has_cells = false;
+    p->tile_ent.release();
+    p->cell_ent.release();
+    p->cell_val.release();
+    if (!rec && g.tile == 32 && m <= (int64_t(1) << 22)) {
+      WPROJ_TRY(build_cells(p, tptr.as<int64_t>(), cum.as<int64_t>(), n_seg, s));
+      p->has_cells = true;
+    }
     WPROJ_TRY(p->grid_partial.alloc(sizeof(float2) * size_t(p->n_chunks) * g.tile * g.tile));
   }
   WPROJ_TRY(p->ytmp.alloc(sizeof(float2) * m));

@@ -1,0 +1,314 @@
+// Gridding X'[q] = sum_k conj(G[k, q]) y_k for G with column indices, from a
+// cell-major copy of G (Eq. 8's adjoint, Section 3.1).
+//
+// The copy holds, for every 32 x 32 grid tile (ascending), the tile's entries
+// sorted by cell and, within a cell, by row: one packed word per entry
+// (row << 10 | cell within the tile; rows < 2^22) and its value.  The gridding
+// then needs no accumulators: a block owns a tile, its warps take equal slices
+// of the tile's entries in windows of 32, and within a window the lanes of one
+// cell are summed by a segmented shuffle scan (cells are sorted, so a cell's
+// entries are adjacent).  A run of one cell that crosses a window boundary is
+// carried to the next window; a run that crosses a warp boundary is merged by
+// thread 0 in warp order.  Every cell therefore gets a fixed summation order
+// (bit-reproducible), each cell is written once, and the tile's empty cells are
+// zeroed by the same block.
+//
+// The copy is built from the tile-ordered segment list by a block per tile:
+// count entries per cell, scan, then place the segments' entries in segment
+// (row) order, one segment at a time.
+#include "plan.h"
+
+namespace wproj {
+
+namespace {
+
+constexpr int kCellWarps = 8;
+constexpr unsigned kCellMask = 1023u;
+
+// exclusive scan of v over a block of 1024 threads; returns the thread's prefix
+__device__ __forceinline__ int block_excl_scan_1024(int v, int *wsum) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int n = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += n;
+  }
+  if (lane == 31) wsum[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    int t = wsum[lane];
+    int ti = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int n = __shfl_up_sync(0xffffffffu, ti, o);
+      if (lane >= o) ti += n;
+    }
+    wsum[lane] = ti - t;
+  }
+  __syncthreads();
+  return wsum[w] + inc - v;
+}
+
+template <int VB>
+__global__ void __launch_bounds__(1024)
+k_cellsort(const int64_t *__restrict__ tptr, const SegMeta *__restrict__ meta, const int32_t *__restrict__ col,
+           const unsigned char *__restrict__ val, const int64_t *__restrict__ tile_ent, int logG, int nT,
+           uint32_t *__restrict__ cell_ent, unsigned char *__restrict__ cell_val) {
+  __shared__ int cnt[1024];
+  __shared__ int base[1024];
+  __shared__ int wsum[32];
+  const int t = blockIdx.x;
+  const int tu = t / nT, tv = t % nT;
+  const int Gm = (1 << logG) - 1;
+  const int64_t s0 = tptr[t], s1 = tptr[t + 1];
+  const int64_t e0 = tile_ent[t];
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  auto cell_of = [&](int q) { return (((q >> logG) - tu * 32) << 5) | ((q & Gm) - tv * 32); };
+  for (int64_t s = s0; s < s1; ++s) {
+    const SegMeta m = meta[s];
+    if ((int)threadIdx.x < meta_cnt(m)) atomicAdd(&cnt[cell_of(col[meta_off(m) + threadIdx.x])], 1);
+  }
+  __syncthreads();
+  base[threadIdx.x] = block_excl_scan_1024(cnt[threadIdx.x], wsum);
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  // place entries segment by segment (rows ascending); the cells of one segment
+  // are distinct, so each cell's counter has one writer per step
+  for (int64_t s = s0; s < s1; ++s) {
+    const SegMeta m = meta[s];
+    if ((int)threadIdx.x < meta_cnt(m)) {
+      const int64_t src = meta_off(m) + threadIdx.x;
+      const int c = cell_of(col[src]);
+      const int64_t dst = e0 + base[c] + cnt[c];
+      cnt[c] += 1;
+      cell_ent[dst] = (uint32_t(m.row) << 10) | uint32_t(c);
+      if constexpr (VB == 8) {
+        reinterpret_cast<float2 *>(cell_val)[dst] = reinterpret_cast<const float2 *>(val)[src];
+      } else {
+        reinterpret_cast<unsigned *>(cell_val)[dst] = reinterpret_cast<const unsigned *>(val)[src];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int VDT>
+__device__ __forceinline__ float2 cell_value(const void *__restrict__ v, int64_t i) {
+  if constexpr (VDT == WPROJ_VAL_F32) {
+    return __ldg(reinterpret_cast<const float2 *>(v) + i);
+  } else if constexpr (VDT == WPROJ_VAL_BF16) {
+    const unsigned raw = __ldg(reinterpret_cast<const unsigned *>(v) + i);
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&raw));
+  } else {
+    const unsigned raw = __ldg(reinterpret_cast<const unsigned *>(v) + i);
+    return __half22float2(*reinterpret_cast<const __half2 *>(&raw));
+  }
+}
+
+// y_k times the row scale of the 16-bit value forms
+__global__ void k_scale_y(int64_t m, const float2 *__restrict__ y, const float *__restrict__ rs,
+                          float2 *__restrict__ ys) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k < m) ys[k] = cscale(y[k], rs[k]);
+}
+
+// y: visibilities, already multiplied by the row scales for 16-bit values.
+// tile_prob / tab (batches): blockIdx.x is a tile of the whole batch
+template <int VDT>
+__global__ void __launch_bounds__(kCellWarps * 32)
+k_grid_cells(const int64_t *__restrict__ tile_ent, const uint32_t *__restrict__ cell_ent,
+             const void *__restrict__ cell_val, const float2 *__restrict__ y,
+             int logG, int nT, const int32_t *__restrict__ tile_prob, const BProb *__restrict__ tab,
+             float2 *__restrict__ Xt2) {
+  __shared__ int h_cell[kCellWarps], t_cell[kCellWarps], h_closed[kCellWarps];
+  __shared__ float2 h_val[kCellWarps], t_val[kCellWarps];
+  int tile = blockIdx.x;
+  const int64_t e0 = tile_ent[tile], e1 = tile_ent[tile + 1];
+  if (tile_prob) {
+    const BProb &P = tab[tile_prob[tile]];
+    logG = P.logG;
+    nT = P.nT;
+    tile -= int(P.tile_off);
+    Xt2 += P.grid_off;
+    y += P.vis_off;
+  }
+  const int G = 1 << logG;
+  const int tu = tile / nT, tv = tile % nT;
+  float2 *out = Xt2 + int64_t(tu * 32) * G + tv * 32;   // cell c at out[(c >> 5) G + (c & 31)]
+  for (int c = threadIdx.x; c < 1024; c += blockDim.x) out[int64_t(c >> 5) * G + (c & 31)] = make_float2(0.f, 0.f);
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t n = e1 - e0;
+  const int64_t a = e0 + n * w / kCellWarps, b = e0 + n * (w + 1) / kCellWarps;
+  int carry_cell = -1;          // run left open by the previous window
+  float2 carry = make_float2(0.f, 0.f);
+  bool head_done = false;       // the warp's first run has been closed
+  // software pipeline: entries and values two windows ahead, y one window ahead
+  auto load_e = [&](int64_t ws) { return ws + lane < b ? __ldg(cell_ent + ws + lane) : 0u; };
+  auto load_v = [&](int64_t ws) {
+    return ws + lane < b ? cell_value<VDT>(cell_val, ws + lane) : make_float2(0.f, 0.f);
+  };
+  auto load_y = [&](int64_t ws, uint32_t e) { return ws + lane < b ? __ldg(y + (e >> 10)) : make_float2(0.f, 0.f); };
+  uint32_t e_cur = load_e(a), e_nxt = load_e(a + 32);
+  float2 v_cur = load_v(a), v_nxt = load_v(a + 32);
+  float2 y_cur = load_y(a, e_cur);
+  for (int64_t ws = a; ws < b; ws += 32) {
+    const uint32_t e_far = load_e(ws + 64);
+    const float2 v_far = load_v(ws + 64);
+    const float2 y_nxt = load_y(ws + 32, e_nxt);
+    const int last_valid = int(b - ws < 32 ? b - ws : 32) - 1;
+    const bool valid = lane <= last_valid;
+    int cell = 2048 + lane;     // invalid lanes form runs of their own
+    float2 t = make_float2(0.f, 0.f);
+    if (valid) {
+      cell = int(e_cur & kCellMask);
+      t = make_float2(v_cur.x * y_cur.x + v_cur.y * y_cur.y, v_cur.x * y_cur.y - v_cur.y * y_cur.x);   // conj(v) y
+    }
+    e_cur = e_nxt;
+    e_nxt = e_far;
+    v_cur = v_nxt;
+    v_nxt = v_far;
+    y_cur = y_nxt;
+    if (carry_cell >= 0 && __shfl_sync(0xffffffffu, cell, 0) != carry_cell) {
+      // the carried run ended exactly at the window boundary
+      if (!head_done) {
+        if (lane == 0) {
+          h_cell[w] = carry_cell;
+          h_val[w] = carry;
+          h_closed[w] = 1;
+        }
+        head_done = true;
+      } else if (lane == 0) {
+        out[int64_t(carry_cell >> 5) * G + (carry_cell & 31)] = carry;
+      }
+      carry_cell = -1;
+    }
+    if (lane == 0 && cell == carry_cell) t = cadd(t, carry);
+    // segmented inclusive scan: sum over the preceding lanes of the same cell
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const float ux = __shfl_up_sync(0xffffffffu, t.x, o);
+      const float uy = __shfl_up_sync(0xffffffffu, t.y, o);
+      const int uc = __shfl_up_sync(0xffffffffu, cell, o);
+      if (lane >= o && uc == cell) t = make_float2(t.x + ux, t.y + uy);
+    }
+    const int next = __shfl_down_sync(0xffffffffu, cell, 1);
+    const bool closes = valid && lane < last_valid && next != cell;
+    unsigned cm = __ballot_sync(0xffffffffu, closes);
+    if (!head_done && cm) {     // the warp's first closed run may have begun in the previous warp
+      const int hl = __ffs(cm) - 1;
+      if (lane == hl) {
+        h_cell[w] = cell;
+        h_val[w] = t;
+      }
+      cm &= cm - 1;
+      head_done = true;
+      if (lane == hl) h_closed[w] = 1;
+    }
+    if ((cm >> lane) & 1u) out[int64_t(cell >> 5) * G + (cell & 31)] = t;
+    carry_cell = __shfl_sync(0xffffffffu, cell, last_valid);
+    carry.x = __shfl_sync(0xffffffffu, t.x, last_valid);
+    carry.y = __shfl_sync(0xffffffffu, t.y, last_valid);
+  }
+  if (lane == 0) {
+    if (!head_done) h_closed[w] = 0;
+    t_cell[w] = (a < b) ? carry_cell : -1;
+    t_val[w] = carry;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // merge the runs that cross warp boundaries, in warp order
+    int oc = -1;
+    float2 ov = make_float2(0.f, 0.f);
+    for (int k = 0; k < kCellWarps; ++k) {
+      if (t_cell[k] < 0) continue;   // no entries
+      if (h_closed[k]) {
+        if (oc == h_cell[k]) {
+          out[int64_t(oc >> 5) * G + (oc & 31)] = cadd(ov, h_val[k]);
+        } else {
+          if (oc >= 0) out[int64_t(oc >> 5) * G + (oc & 31)] = ov;
+          out[int64_t(h_cell[k] >> 5) * G + (h_cell[k] & 31)] = h_val[k];
+        }
+        oc = t_cell[k];
+        ov = t_val[k];
+      } else if (oc == t_cell[k]) {   // one run spans the whole slice
+        ov = cadd(ov, t_val[k]);
+      } else {
+        if (oc >= 0) out[int64_t(oc >> 5) * G + (oc & 31)] = ov;
+        oc = t_cell[k];
+        ov = t_val[k];
+      }
+    }
+    if (oc >= 0) out[int64_t(oc >> 5) * G + (oc & 31)] = ov;
+  }
+}
+
+__global__ void k_tile_ent(int n_tiles, const int64_t *__restrict__ tptr, const int64_t *__restrict__ cum,
+                           int64_t n_seg, int64_t nnz, int64_t *__restrict__ tile_ent) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t > n_tiles) return;
+  const int64_t s = tptr[t];
+  tile_ent[t] = s < n_seg ? cum[s] : nnz;
+}
+
+}  // namespace
+
+// Cell-major copy of a plan's column-format G (needs p->m <= 2^22, the tile
+// segment list in p->seg_meta and its tile ranges tptr with entry prefix cum).
+wproj_status build_cells(wproj_plan *p, const int64_t *tptr, const int64_t *cum, int64_t n_seg, cudaStream_t s) {
+  const int n_tiles = p->g.nT * p->g.nT;
+  const int vb = p->g.value_dtype == WPROJ_VAL_F32 ? 8 : 4;
+  WPROJ_TRY(p->tile_ent.alloc(sizeof(int64_t) * (n_tiles + 1)));
+  WPROJ_TRY(p->cell_ent.alloc(sizeof(uint32_t) * std::max<int64_t>(1, p->nnz)));
+  WPROJ_TRY(p->cell_val.alloc(int64_t(vb) * std::max<int64_t>(1, p->nnz)));
+  k_tile_ent<<<ceil_div(n_tiles + 1, 256), 256, 0, s>>>(n_tiles, tptr, cum, n_seg, p->nnz,
+                                                       p->tile_ent.as<int64_t>());
+  WPROJ_CHECK_LAUNCH("tile entries");
+  const int logG = ilog2(p->g.G);
+  if (vb == 8) {
+    k_cellsort<8><<<n_tiles, 1024, 0, s>>>(tptr, p->seg_meta.as<SegMeta>(), p->col.as<int32_t>(),
+                                          p->val.as<unsigned char>(), p->tile_ent.as<int64_t>(), logG, p->g.nT,
+                                          p->cell_ent.as<uint32_t>(), p->cell_val.as<unsigned char>());
+  } else {
+    k_cellsort<4><<<n_tiles, 1024, 0, s>>>(tptr, p->seg_meta.as<SegMeta>(), p->col.as<int32_t>(),
+                                          p->val.as<unsigned char>(), p->tile_ent.as<int64_t>(), logG, p->g.nT,
+                                          p->cell_ent.as<uint32_t>(), p->cell_val.as<unsigned char>());
+  }
+  WPROJ_CHECK_LAUNCH("cell sort");
+  return WPROJ_OK;
+}
+
+wproj_status grid_cells(wproj_plan *p, const float2 *y, float2 *Xt2, cudaStream_t s) {
+  const int n_tiles = p->g.nT * p->g.nT;
+  const int logG = ilog2(p->g.G);
+  if (p->g.value_dtype != WPROJ_VAL_F32) {
+    k_scale_y<<<ceil_div(p->m, 256), 256, 0, s>>>(p->m, y, p->row_scale.as<float>(), p->ytmp.as<float2>());
+    WPROJ_CHECK_LAUNCH("scaled visibilities");
+    y = p->ytmp.as<float2>();
+    p->launches += 1;
+  }
+#define GC(VDT)                                                                                            \
+  k_grid_cells<VDT><<<n_tiles, kCellWarps * 32, 0, s>>>(p->tile_ent.as<int64_t>(), p->cell_ent.as<uint32_t>(), \
+                                                        p->cell_val.ptr, y, logG, p->g.nT, nullptr, nullptr,  \
+                                                        Xt2)
+  switch (p->g.value_dtype) {
+    case WPROJ_VAL_F32: GC(WPROJ_VAL_F32); break;
+    case WPROJ_VAL_BF16: GC(WPROJ_VAL_BF16); break;
+    default: GC(WPROJ_VAL_F16);
+  }
+#undef GC
+  WPROJ_CHECK_LAUNCH("grid (cells)");
+  return WPROJ_OK;
+}
+
+wproj_status batch_grid_cells(const BatchOps &b, const float2 *y, float2 *Xt2, cudaStream_t s) {
+  k_grid_cells<WPROJ_VAL_F32><<<(unsigned)b.n_tiles, kCellWarps * 32, 0, s>>>(
+      b.tile_ent, b.cell_ent, b.cell_val, y, 0, 0, b.tile_prob, b.tab, Xt2);
+  WPROJ_CHECK_LAUNCH("batch grid (cells)");
+  return WPROJ_OK;
+}
+
+}  // namespace wproj

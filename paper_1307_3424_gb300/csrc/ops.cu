@@ -247,6 +247,9 @@ wproj_status grid(wproj_plan *p, const float2 *y, float2 *Xt2, cudaStream_t s) {
   } while (0)
     if (p->fmt == WPROJ_INDEX_TILE_MASK) {
       WPROJ_TRY(grid_stream(p, y, s));
+    } else if (p->has_cells) {
+      p->launches -= 1;   // one kernel, no chunk reduction
+      return grid_cells(p, y, Xt2, s);
     } else {
       switch (g.value_dtype) {
         case WPROJ_VAL_F32: LAUNCH_GRID(WPROJ_VAL_F32); break;
@@ -295,6 +298,7 @@ wproj_status batch_degrid(const BatchOps &b, const float2 *Xt, float2 *partial, 
 }
 
 wproj_status batch_grid(const BatchOps &b, const float2 *y, float2 *partial, float2 *Xt2, cudaStream_t s) {
+  if (b.cell_ent) return batch_grid_cells(b, y, Xt2, s);
   const size_t smem = sizeof(float2) * kGridWarps * kTile * kTile;
   WPROJ_CUDA(cudaFuncSetAttribute(k_grid<WPROJ_VAL_F32, kGridWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));

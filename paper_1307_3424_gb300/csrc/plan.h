@@ -64,6 +64,10 @@ struct BatchOps {
   const int64_t *chunk_lo = nullptr, *chunk_hi = nullptr;
   const SegMeta *meta = nullptr;         // tile order, entry offsets and rows of the batch
   const BProb *tab = nullptr;
+  // cell-major copy (rows local to their problem); null when absent
+  const int64_t *tile_ent = nullptr;
+  const uint32_t *cell_ent = nullptr;
+  const void *cell_val = nullptr;
 };
 
 // Timing accumulator for one class of kernels.
@@ -122,6 +126,12 @@ struct wproj_plan {
   wproj::DevBuf seg_row;     // int32[n_seg]
   // gridding: segments sorted by tile (rows ascending), chunked by nnz
   wproj::DevBuf seg_meta;    // SegMeta[n_seg] in tile-sorted order (COLUMNS)
+  // cell-major copy for the gridding (COLUMNS, m <= 2^22): per tile its entries
+  // sorted by cell then row, packed (row << 10 | cell) with their values
+  bool has_cells = false;
+  wproj::DevBuf tile_ent;    // int64[nT*nT+1] first entry of each tile
+  wproj::DevBuf cell_ent;    // uint32[nnz]
+  wproj::DevBuf cell_val;    // values[nnz]
   int64_t n_chunks = 0;
   wproj::DevBuf chunk_tile;  // int32[n_chunks]
   wproj::DevBuf chunk_lo;    // int64[n_chunks]  first position in the tile order (seg_meta /
@@ -195,6 +205,11 @@ wproj_status degrid_into(wproj_plan *p, const float2 *Xt, float2 *partial, float
 wproj_status csr_rows(const wproj_plan *p, int64_t k0, int64_t k1, int32_t *col_out, void *val_out,
                       cudaStream_t s);
 int64_t degrid_partials(const wproj_plan *p);   // partial sums degridding needs
+
+// cells.cu: cell-major gridding of the column format
+wproj_status build_cells(wproj_plan *p, const int64_t *tptr, const int64_t *cum, int64_t n_seg, cudaStream_t s);
+wproj_status grid_cells(wproj_plan *p, const float2 *y, float2 *Xt2, cudaStream_t s);
+wproj_status batch_grid_cells(const BatchOps &b, const float2 *y, float2 *Xt2, cudaStream_t s);
 
 // batches (column format)
 wproj_status batch_degrid(const BatchOps &b, const float2 *Xt, float2 *partial, float2 *y, cudaStream_t s);

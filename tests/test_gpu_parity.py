@@ -171,8 +171,10 @@ def test_build_rejects_bad_input(wp):
 # ---- operators ------------------------------------------------------------------------
 
 
-@pytest.mark.parametrize("N,M,box,vdt", [(16, 60, None, "f32"), (32, 200, None, "f32"), (64, 300, 32, "f32"),
-                                         (128, 150, None, "f32"), (64, 200, "rule", "f32")])
+# N = 8 (a 16 x 16 grid, one 16 x 16 tile) takes the chunked shared-memory
+# gridding; the others the cell-major or tile-stream gridding
+@pytest.mark.parametrize("N,M,box,vdt", [(8, 20, None, "f32"), (16, 60, None, "f32"), (32, 200, None, "f32"),
+                                         (64, 300, 32, "f32"), (128, 150, None, "f32"), (64, 200, "rule", "f32")])
 def test_phi_and_adjoint_match_oracle_at_e1(wp, N, M, box, vdt):
     rng = np.random.default_rng(N)
     uvw = synth.random_uvw(rng, M, N, L, 1.0)
