@@ -261,6 +261,15 @@ void wproj_dr_defaults(wproj_dr_params *prm);
 const char *wproj_last_error(void);
 const char *wproj_version(void);
 
+/* ---- dense BF16 GEMM on the tensor cores ------------------------------------------
+ * C[m x n] = A[m x k] B[n x k]^T (+ bias[n]): A, B row-major BF16, C row-major FP32
+ * (out_bf16 = 0) or BF16, FP32 accumulation, on the tcgen05 tensor cores.  The
+ * dense contraction of the learned-kernel MLP, exported for testing.
+ * m, n multiples of 128, k a multiple of 64, else WPROJ_ERR_INVALID_ARG.
+ * bias may be NULL.  Synchronous; WPROJ_ERR_TIMEOUT if a tensor-core wait ran out. */
+wproj_status wproj_gemm_bf16(int32_t m, int32_t n, int32_t k, const void *a, const void *b, const float *bias,
+                             void *c, int32_t out_bf16, void *stream);
+
 /* ---- batches of independent problems ------------------------------------------
  * Many imaging problems of uneven N and M (each a full Eq. 7 problem with its own
  * Phi, Section 3) held in one object.  Every stage of Phi, Phi^H and the

@@ -211,6 +211,10 @@ wproj_status build_cells(wproj_plan *p, const int64_t *tptr, const int64_t *cum,
 wproj_status grid_cells(wproj_plan *p, const float2 *y, float2 *Xt2, cudaStream_t s);
 wproj_status batch_grid_cells(const BatchOps &b, const float2 *y, float2 *Xt2, cudaStream_t s);
 
+// gemm.cu: C = A B^T (+ bias) on the tcgen05 tensor cores, BF16 in, FP32 accumulate
+wproj_status gemm_bf16_tn(int M, int N, int K, const __nv_bfloat16 *A, const __nv_bfloat16 *B, const float *bias,
+                          void *C, bool out_bf16, int *err, cudaStream_t s);
+
 // batches (column format)
 wproj_status batch_degrid(const BatchOps &b, const float2 *Xt, float2 *partial, float2 *y, cudaStream_t s);
 wproj_status batch_grid(const BatchOps &b, const float2 *y, float2 *partial, float2 *Xt2, cudaStream_t s);

@@ -30,7 +30,7 @@ EXPORTED = [
     "wproj_dr_state_set", "wproj_phi_noalloc", "wproj_csr_rows",
     "wproj_batch_create", "wproj_batch_destroy", "wproj_batch_build", "wproj_batch_tune",
     "wproj_batch_set_schedule", "wproj_batch_phi", "wproj_batch_phi_adj", "wproj_batch_solve_bpdn",
-    "wproj_batch_get_info",
+    "wproj_batch_get_info", "wproj_gemm_bf16",
 ]
 
 
@@ -135,6 +135,7 @@ def lib() -> ctypes.CDLL:
         "wproj_batch_phi_adj": [vp, vp, vp, vp],
         "wproj_batch_solve_bpdn": [vp, vp, P(dbl), P(DRParams), vp, vp],
         "wproj_batch_get_info": [vp, P(BatchInfo)],
+        "wproj_gemm_bf16": [i32, i32, i32, vp, vp, vp, vp, i32, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -488,3 +489,17 @@ class Batch:
 
     def split_vis(self, y: torch.Tensor):
         return [y[a:b] for a, b in zip(self.vis_off[:-1], self.vis_off[1:])]
+
+
+def gemm_bf16(a: torch.Tensor, b: torch.Tensor, bias: torch.Tensor | None = None, out_bf16: bool = False,
+              stream=None) -> torch.Tensor:
+    """a (m, k) and b (n, k) BF16 on the device: a @ b.T (+ bias) on the tensor cores."""
+    if a.dtype != torch.bfloat16 or b.dtype != torch.bfloat16 or a.shape[1] != b.shape[1]:
+        raise WprojError(ERR_INVALID_ARG, "a (m, k) and b (n, k) must be bfloat16")
+    m, k = a.shape
+    n = b.shape[0]
+    c = torch.empty((m, n), dtype=torch.bfloat16 if out_bf16 else torch.float32, device=a.device)
+    _check(lib().wproj_gemm_bf16(m, n, k, _ptr(a.contiguous()), _ptr(b.contiguous()),
+                                 _ptr(bias) if bias is not None else None, _ptr(c), 1 if out_bf16 else 0,
+                                 _stream(stream)))
+    return c
