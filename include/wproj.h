@@ -270,6 +270,48 @@ const char *wproj_version(void);
 wproj_status wproj_gemm_bf16(int32_t m, int32_t n, int32_t k, const void *a, const void *b, const float *bias,
                              void *c, int32_t out_bf16, void *stream);
 
+/* ---- learned kernels ----------------------------------------------------------
+ * An MLP mapping a visibility's (w, sub-grid offset) to its w-kernel on a fixed
+ * 32 x 32 window of grid cells plus a support mask, trained on kernels of the
+ * plain build (which stays the reference and the fallback):
+ *   x0 = (w_c/2 - 1, 2 du - 1, 2 dv - 1), w_c = |w| L^2 / 2 grid cells, (du, dv)
+ *        the sub-grid offset of (u, v) / du_cell;
+ *   h1 = GELU(W1 x0 + b1), h2 = GELU(W2 h1 + b2), h3 = GELU(W3 h2 + b3)  (256 each)
+ *   y  = W4 h3 + b4  (3072): y[2(32a+b)], y[2(32a+b)+1] the real and imaginary
+ *        parts of the kernel at window cell (a, b) = grid cell (j0 - 16 + a,
+ *        j0 - 16 + b) mod G scaled by 1/sqrt(E_kb) (E_kb = prod over axes of
+ *        sum_t kb(delta - t)^2), y[2048 + 32a + b] the logit of (a, b) being in
+ *        the support;
+ *   loss = mean over values of (y - t)^2 + mask_weight * mean BCE(logit, mask).
+ * GELU is the erf form.  Layers 2-4 and their gradients run as BF16 GEMMs on the
+ * tensor cores with FP32 accumulation; parameters, Adam and reductions are FP32.
+ * Parameters are one flat FP32 vector: W1 (256x3), b1, W2 (256x256), b2, W3, b3,
+ * W4 (3072x256), b4, matrices row-major [out][in]. */
+typedef struct wproj_mlp wproj_mlp;
+int64_t wproj_mlp_num_params(void);
+wproj_status wproj_mlp_create(wproj_mlp **out);   /* parameters zero until set */
+wproj_status wproj_mlp_destroy(wproj_mlp *n);
+/* params: wproj_mlp_num_params() floats, host or device; set resets Adam. */
+wproj_status wproj_mlp_set_params(wproj_mlp *n, const float *params, void *stream);
+wproj_status wproj_mlp_get_params(const wproj_mlp *n, float *params, void *stream);
+/* Training data from a built plan (complex64, column indices), rows of uvw
+ * (device, m x 3 as given to wproj_build_kernels): x0 (m x 3), tval (m x 2048),
+ * tmask (m x 1024), device FP32. */
+wproj_status wproj_mlp_targets(const wproj_plan *p, const double *uvw, float *x0, float *tval, float *tmask,
+                               void *stream);
+/* y (m x 3072) = network(x0) for m rows, m a multiple of 128.  Synchronous. */
+wproj_status wproj_mlp_forward(wproj_mlp *n, const float *x0, int64_t m, float *y, void *stream);
+/* loss (host) and, when grad (device or host, num_params floats) is given, the
+ * gradient of the loss over the m rows (a multiple of 128, <= 65536).  Synchronous. */
+wproj_status wproj_mlp_gradients(wproj_mlp *n, const float *x0, const float *tval, const float *tmask, int64_t m,
+                                 double mask_weight, double *loss, float *grad, void *stream);
+/* steps of Adam (beta 0.9, 0.999, eps 1e-8, learning rate lr) on batches of
+ * `batch` consecutive rows, cycling through m rows (batch | m); losses (host,
+ * steps floats, may be NULL) receives each step's loss.  Synchronous. */
+wproj_status wproj_mlp_train(wproj_mlp *n, const float *x0, const float *tval, const float *tmask, int64_t m,
+                             int32_t batch, int32_t steps, double lr, double mask_weight, float *losses,
+                             void *stream);
+
 /* ---- batches of independent problems ------------------------------------------
  * Many imaging problems of uneven N and M (each a full Eq. 7 problem with its own
  * Phi, Section 3) held in one object.  Every stage of Phi, Phi^H and the

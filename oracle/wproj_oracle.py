@@ -9,8 +9,8 @@ Everything here is plain, slow and written to be checked against the paper by
 eye: complex128 / float64 NumPy, with numpy.fft and scipy.sparse as the only
 library primitives.  Each function cites the passage it follows.
 
-Model (the spec form of the paper's operator, Eq. 8 with continuous
-(u, v) and a Kaiser-Bessel gridding kernel):
+Model (the paper's operator, Eq. 8, with continuous (u, v) and a
+Kaiser-Bessel gridding kernel):
 
     Phi = G . F . Z . A
 
@@ -50,7 +50,7 @@ import scipy.sparse
 import scipy.special
 
 # ----------------------------------------------------------------------------
-# Kaiser-Bessel gridding kernel and its Fourier transform (spec gridding;
+# Kaiser-Bessel gridding kernel and its Fourier transform (the gridding used here;
 # Jackson et al. 1991, Beatty et al. 2005).  Not in the paper itself, which
 # keeps visibilities on the grid (Section 2.2).
 # ----------------------------------------------------------------------------

@@ -91,13 +91,6 @@ int box_tiles(int S, const GridGeom &g) {
   return per * per;
 }
 
-__device__ __forceinline__ double kb_dev(double t, int W, double beta) {
-  const double r = 2.0 * t / W;
-  const double arg = 1.0 - r * r;
-  if (arg < 0.0) return 0.0;
-  return cyl_bessel_i0(beta * sqrt(arg));
-}
-
 // ---- row plan -------------------------------------------------------------------
 
 __global__ void k_row_plan(const double *__restrict__ uvw, int64_t m, GridGeom g,

@@ -45,6 +45,14 @@ __device__ __forceinline__ float abs2_rn(float2 z) {
   return __fadd_rn(__fmul_rn(z.x, z.x), __fmul_rn(z.y, z.y));
 }
 
+// Kaiser-Bessel gridding kernel of support W (unnormalised), t in cells
+__device__ __forceinline__ double kb_dev(double t, int W, double beta) {
+  const double r = 2.0 * t / W;
+  const double arg = 1.0 - r * r;
+  if (arg < 0.0) return 0.0;
+  return cyl_bessel_i0(beta * sqrt(arg));
+}
+
 // ---- FP64 block reductions (fixed order: bit-reproducible) ---------------------
 __device__ __forceinline__ double warp_sum_d(double v) {
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

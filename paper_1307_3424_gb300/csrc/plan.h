@@ -215,6 +215,9 @@ wproj_status batch_grid_cells(const BatchOps &b, const float2 *y, float2 *Xt2, c
 wproj_status gemm_bf16_tn(int M, int N, int K, const __nv_bfloat16 *A, const __nv_bfloat16 *B, const float *bias,
                           void *C, bool out_bf16, int *err, cudaStream_t s);
 
+// mlp.cu: the learned-kernel network
+int64_t mlp_num_params();
+
 // batches (column format)
 wproj_status batch_degrid(const BatchOps &b, const float2 *Xt, float2 *partial, float2 *y, cudaStream_t s);
 wproj_status batch_grid(const BatchOps &b, const float2 *y, float2 *partial, float2 *Xt2, cudaStream_t s);

@@ -229,3 +229,34 @@ def make_batch(bw: BatchWorkload, seed: int = 0, n_problems: int | None = None,
         uvw = np.ascontiguousarray(np.concatenate([uv, w[:, None]], axis=1))
         out.append(Problem(wl, L, x, uvw, wc, rng))
     return out
+
+
+def mlp_init_params(seed: int = 0) -> np.ndarray:
+    """Initial parameters of the learned-kernel network (flat float32, layout of
+    include/wproj.h): weights N(0, 1/fan_in) (1/3 for the 3-wide input layer),
+    biases zero."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    parts = []
+    for out_f, in_f in ((256, 3), (256, 256), (256, 256), (3072, 256)):
+        parts.append(rng.standard_normal(out_f * in_f) / math.sqrt(in_f))
+        parts.append(np.zeros(out_f))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def mlp_samples(m: int, seed: int, wc_max: float = 4.0) -> tuple[np.ndarray, np.ndarray]:
+    """uvw rows for training the learned-kernel network on an N-pixel grid:
+    sub-grid offsets U[0,1)^2 around random cells, w_c ~ U[0, wc_max] cells
+    (h = 2 w_c).  Returns (offsets, w_c); `mlp_uvw` places them on a grid."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.uniform(0.0, 1.0, (m, 2)), rng.uniform(0.0, wc_max, m)
+
+
+def mlp_uvw(offsets: np.ndarray, wc: np.ndarray, N: int, L: float, seed: int = 1) -> np.ndarray:
+    """(u, v, w) in wavelengths for cells drawn uniformly inside |g| < N/2 - 16."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    m = wc.shape[0]
+    du = 1.0 / (2.0 * L)
+    cells = rng.integers(-(N // 2 - 16), N // 2 - 16, (m, 2))
+    uv = (cells + offsets) * du
+    w = 2.0 * wc / (L * L)
+    return np.ascontiguousarray(np.concatenate([uv, w[:, None]], axis=1))

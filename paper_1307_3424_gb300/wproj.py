@@ -30,7 +30,9 @@ EXPORTED = [
     "wproj_dr_state_set", "wproj_phi_noalloc", "wproj_csr_rows",
     "wproj_batch_create", "wproj_batch_destroy", "wproj_batch_build", "wproj_batch_tune",
     "wproj_batch_set_schedule", "wproj_batch_phi", "wproj_batch_phi_adj", "wproj_batch_solve_bpdn",
-    "wproj_batch_get_info", "wproj_gemm_bf16",
+    "wproj_batch_get_info", "wproj_gemm_bf16", "wproj_mlp_num_params", "wproj_mlp_create",
+    "wproj_mlp_destroy", "wproj_mlp_set_params", "wproj_mlp_get_params", "wproj_mlp_targets",
+    "wproj_mlp_forward", "wproj_mlp_gradients", "wproj_mlp_train",
 ]
 
 
@@ -136,11 +138,21 @@ def lib() -> ctypes.CDLL:
         "wproj_batch_solve_bpdn": [vp, vp, P(dbl), P(DRParams), vp, vp],
         "wproj_batch_get_info": [vp, P(BatchInfo)],
         "wproj_gemm_bf16": [i32, i32, i32, vp, vp, vp, vp, i32, vp],
+        "wproj_mlp_create": [P(vp)],
+        "wproj_mlp_destroy": [vp],
+        "wproj_mlp_set_params": [vp, vp, vp],
+        "wproj_mlp_get_params": [vp, vp, vp],
+        "wproj_mlp_targets": [vp, vp, vp, vp, vp, vp],
+        "wproj_mlp_forward": [vp, vp, i64, vp, vp],
+        "wproj_mlp_gradients": [vp, vp, vp, vp, i64, dbl, P(dbl), vp, vp],
+        "wproj_mlp_train": [vp, vp, vp, vp, i64, i32, i32, dbl, dbl, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
         f.argtypes = args
         f.restype = ctypes.c_int
+    L.wproj_mlp_num_params.argtypes = []
+    L.wproj_mlp_num_params.restype = ctypes.c_int64
     L.wproj_dr_defaults.argtypes = [P(DRParams)]
     L.wproj_dr_defaults.restype = None
     L.wproj_last_error.restype = ctypes.c_char_p
@@ -503,3 +515,71 @@ def gemm_bf16(a: torch.Tensor, b: torch.Tensor, bias: torch.Tensor | None = None
                                  _ptr(bias) if bias is not None else None, _ptr(c), 1 if out_bf16 else 0,
                                  _stream(stream)))
     return c
+
+
+class MLP:
+    """The learned-kernel network (include/wproj.h, wproj_mlp_*): (w, offset) ->
+    32 x 32 kernel window (2048 values) + support logits (1024)."""
+
+    N_IN, N_HID, N_VAL, N_MASK = 3, 256, 2048, 1024
+
+    def __init__(self, params: torch.Tensor | None = None):
+        self._h = ctypes.c_void_p()
+        _check(lib().wproj_mlp_create(ctypes.byref(self._h)))
+        self.n_params = int(lib().wproj_mlp_num_params())
+        if params is not None:
+            self.set_params(params)
+
+    def close(self):
+        if self._h:
+            lib().wproj_mlp_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, p: torch.Tensor, stream=None):
+        if p.dtype != torch.float32 or p.numel() != self.n_params:
+            raise WprojError(ERR_INVALID_ARG, f"params must be {self.n_params} float32 values")
+        p = p.contiguous()
+        _check(lib().wproj_mlp_set_params(self._h, ctypes.c_void_p(p.data_ptr()), _stream(stream)))
+
+    def params(self, stream=None) -> torch.Tensor:
+        p = torch.empty(self.n_params, dtype=torch.float32)
+        _check(lib().wproj_mlp_get_params(self._h, ctypes.c_void_p(p.data_ptr()), _stream(stream)))
+        return p
+
+    @staticmethod
+    def targets(plan: "Plan", uvw: torch.Tensor, stream=None):
+        dev = uvw.device
+        m = uvw.shape[0]
+        x0 = torch.empty((m, 3), dtype=torch.float32, device=dev)
+        tv = torch.empty((m, 2048), dtype=torch.float32, device=dev)
+        tm = torch.empty((m, 1024), dtype=torch.float32, device=dev)
+        _check(lib().wproj_mlp_targets(plan._h, _ptr(uvw.contiguous()), _ptr(x0), _ptr(tv), _ptr(tm),
+                                       _stream(stream)))
+        return x0, tv, tm
+
+    def forward(self, x0: torch.Tensor, stream=None) -> torch.Tensor:
+        m = x0.shape[0]
+        y = torch.empty((m, 3072), dtype=torch.float32, device=x0.device)
+        _check(lib().wproj_mlp_forward(self._h, _ptr(x0.contiguous()), m, _ptr(y), _stream(stream)))
+        return y
+
+    def gradients(self, x0, tv, tm, mask_weight: float = 0.1, stream=None):
+        loss = ctypes.c_double()
+        g = torch.empty(self.n_params, dtype=torch.float32, device=x0.device)
+        _check(lib().wproj_mlp_gradients(self._h, _ptr(x0.contiguous()), _ptr(tv.contiguous()),
+                                         _ptr(tm.contiguous()), x0.shape[0], float(mask_weight),
+                                         ctypes.byref(loss), _ptr(g), _stream(stream)))
+        return loss.value, g
+
+    def train(self, x0, tv, tm, batch: int, steps: int, lr: float, mask_weight: float = 0.1, stream=None):
+        losses = (ctypes.c_float * max(1, steps))()
+        _check(lib().wproj_mlp_train(self._h, _ptr(x0.contiguous()), _ptr(tv.contiguous()), _ptr(tm.contiguous()),
+                                     x0.shape[0], int(batch), int(steps), float(lr), float(mask_weight), losses,
+                                     _stream(stream)))
+        return list(losses)[:steps]
