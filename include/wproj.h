@@ -312,6 +312,24 @@ wproj_status wproj_mlp_train(wproj_mlp *n, const float *x0, const float *tval, c
                              int32_t batch, int32_t steps, double lr, double mask_weight, float *losses,
                              void *stream);
 
+/* Learned build: G by the plain build (COLUMNS, complex64 plans), then every
+ * row's kernel predicted by the network and judged against the plain one on the
+ * 32 x 32 window: a row takes the predicted values on its support only when the
+ * relative L2 error over the window is <= rel_l2_max, the predicted support
+ * holds >= e of the kernel energy and no plain entry lies outside the window;
+ * every other row keeps the plain kernel (the fallback).  row_err (device, m
+ * floats, may be NULL) receives each row's relative L2 error.  Synchronous. */
+typedef struct {
+  int64_t rows;
+  int64_t learned;        /* rows that took the predicted kernel */
+  double rel_l2_mean;     /* mean relative L2 error of the predictions */
+  double plain_ms;        /* wall time of the plain build */
+  double learned_ms;      /* wall time of inference and judging */
+} wproj_learned_info;
+wproj_status wproj_build_kernels_learned(wproj_plan *p, wproj_mlp *n, const double *uvw, int64_t m, double e,
+                                         double rel_l2_max, float *row_err, wproj_learned_info *info,
+                                         void *stream);
+
 /* ---- batches of independent problems ------------------------------------------
  * Many imaging problems of uneven N and M (each a full Eq. 7 problem with its own
  * Phi, Section 3) held in one object.  Every stage of Phi, Phi^H and the

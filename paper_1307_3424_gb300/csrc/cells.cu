@@ -281,6 +281,42 @@ wproj_status build_cells(wproj_plan *p, const int64_t *tptr, const int64_t *cum,
   return WPROJ_OK;
 }
 
+namespace {
+// first segment of every tile from the plan's chunk list
+__global__ void k_tptr_from_chunks(int n_tiles, const int64_t *__restrict__ chunk_lo,
+                                   const int32_t *__restrict__ tile_chunk_ptr, int64_t n_seg,
+                                   int64_t *__restrict__ tptr) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n_tiles) tptr[t] = chunk_lo[tile_chunk_ptr[t]];
+  if (t == n_tiles) tptr[t] = n_seg;
+}
+}  // namespace
+
+// Refresh the cell-major copy after the row-major values changed (same support).
+wproj_status rebuild_cells(wproj_plan *p, cudaStream_t s) {
+  if (!p->has_cells) return WPROJ_OK;
+  const int n_tiles = p->g.nT * p->g.nT;
+  DevBuf tptr;
+  WPROJ_TRY(tptr.alloc(sizeof(int64_t) * (n_tiles + 1)));
+  k_tptr_from_chunks<<<ceil_div(n_tiles + 1, 256), 256, 0, s>>>(n_tiles, p->chunk_lo.as<int64_t>(),
+                                                               p->tile_chunk_ptr.as<int32_t>(), p->n_seg,
+                                                               tptr.as<int64_t>());
+  WPROJ_CHECK_LAUNCH("tile ranges");
+  const int logG = ilog2(p->g.G);
+  if (p->g.value_dtype == WPROJ_VAL_F32) {
+    k_cellsort<8><<<n_tiles, 1024, 0, s>>>(tptr.as<int64_t>(), p->seg_meta.as<SegMeta>(), p->col.as<int32_t>(),
+                                          p->val.as<unsigned char>(), p->tile_ent.as<int64_t>(), logG, p->g.nT,
+                                          p->cell_ent.as<uint32_t>(), p->cell_val.as<unsigned char>());
+  } else {
+    k_cellsort<4><<<n_tiles, 1024, 0, s>>>(tptr.as<int64_t>(), p->seg_meta.as<SegMeta>(), p->col.as<int32_t>(),
+                                          p->val.as<unsigned char>(), p->tile_ent.as<int64_t>(), logG, p->g.nT,
+                                          p->cell_ent.as<uint32_t>(), p->cell_val.as<unsigned char>());
+  }
+  WPROJ_CHECK_LAUNCH("cell sort");
+  WPROJ_CUDA(cudaStreamSynchronize(s));
+  return WPROJ_OK;
+}
+
 wproj_status grid_cells(wproj_plan *p, const float2 *y, float2 *Xt2, cudaStream_t s) {
   const int n_tiles = p->g.nT * p->g.nT;
   const int logG = ilog2(p->g.G);

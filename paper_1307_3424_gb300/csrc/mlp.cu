@@ -16,12 +16,14 @@
 // gradients fed to GEMMs are rounded to BF16.  GELU is the erf form.
 #include <math.h>
 
+#include <chrono>
 #include <new>
 #include <vector>
 
 #include "plan.h"
 
 namespace wproj {
+wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, double e, cudaStream_t s);
 namespace mlpk {
 constexpr int kIn = 3, kH = 256, kOutV = 2048, kOutM = 1024, kOut = kOutV + kOutM, kWin = 32;
 constexpr int64_t oW1 = 0, oB1 = oW1 + kH * kIn, oW2 = oB1 + kH, oB2 = oW2 + kH * kH, oW3 = oB2 + kH,
@@ -315,9 +317,159 @@ __global__ void k_targets(int64_t m, const double *__restrict__ uvw, const int64
   }
 }
 
+// Network input of every row (the x0 of k_targets).
+__global__ void k_features(int64_t m, const double *__restrict__ uvw, double du, double L, float *__restrict__ x0) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= m) return;
+  const double gu = uvw[3 * k] / du, gv = uvw[3 * k + 1] / du;
+  const double wc = fabs(uvw[3 * k + 2]) * L * L / 2.0;
+  x0[k * 3] = float(wc / 2.0 - 1.0);
+  x0[k * 3 + 1] = float(2.0 * (gu - floor(gu)) - 1.0);
+  x0[k * 3 + 2] = float(2.0 * (gv - floor(gv)) - 1.0);
+}
+
+// Judge the predicted kernels of rows [r0, r0 + nr) against the plain ones and
+// take the predicted values where they pass: rel. L2 over the window <= relmax,
+// the predicted support holding >= e of the kernel energy (measured on the
+// plain kernel), and no plain entry outside the window.  Block per row.
+__global__ void __launch_bounds__(256)
+k_judge(int64_t r0, const double *__restrict__ uvw, const int64_t *__restrict__ row_ptr,
+        const int32_t *__restrict__ col, float2 *__restrict__ val, const float *__restrict__ Y, int G, double du,
+        int W, double beta, double e, double relmax, float *__restrict__ row_err, int8_t *__restrict__ pass) {
+  __shared__ float2 T[kWin * kWin];
+  __shared__ int outside;
+  const int64_t k = r0 + blockIdx.x;
+  const float *y = Y + int64_t(blockIdx.x) * kOut;
+  const double gu = uvw[3 * k] / du, gv = uvw[3 * k + 1] / du;
+  const double fu = floor(gu), fv = floor(gv);
+  const double dlu = gu - fu, dlv = gv - fv;
+  double eu = 0, ev = 0;
+  for (int t = -W / 2 + 1; t <= W / 2; ++t) {
+    const double a = kb_dev(dlu - t, W, beta), b = kb_dev(dlv - t, W, beta);
+    eu += a * a;
+    ev += b * b;
+  }
+  const double ekb = eu * ev;
+  const float sc = float(sqrt(ekb));
+  for (int i = threadIdx.x; i < kWin * kWin; i += blockDim.x) T[i] = make_float2(0.f, 0.f);
+  if (threadIdx.x == 0) outside = 0;
+  __syncthreads();
+  const int ou = ((int(fu) - kWin / 2) % G + G) % G, ov = ((int(fv) - kWin / 2) % G + G) % G;
+  const int64_t lo = row_ptr[k], hi = row_ptr[k + 1];
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const int q = col[i];
+    const int a = ((q / G - ou) % G + G) % G, b = ((q % G - ov) % G + G) % G;
+    if (a < kWin && b < kWin) T[a * kWin + b] = val[i];
+    else outside = 1;
+  }
+  __syncthreads();
+  double d2 = 0, t2 = 0, sup = 0;
+  for (int i = threadIdx.x; i < kWin * kWin; i += blockDim.x) {
+    const float2 t = T[i];
+    const float px = y[2 * i] * sc, py = y[2 * i + 1] * sc;
+    d2 += double(px - t.x) * (px - t.x) + double(py - t.y) * (py - t.y);
+    const double tt = double(t.x) * t.x + double(t.y) * t.y;
+    t2 += tt;
+    if (y[kOutV + i] > 0.f) sup += tt;
+  }
+  d2 = block_sum_d<256>(d2);
+  t2 = block_sum_d<256>(t2);
+  sup = block_sum_d<256>(sup);
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    const double r = t2 > 0 ? sqrt(d2 / t2) : 1.0;
+    ok = (!outside && r <= relmax && sup >= e * ekb) ? 1 : 0;
+    if (row_err) row_err[k] = float(r);
+    pass[k] = int8_t(ok);
+  }
+  __syncthreads();
+  if (!ok) return;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const int q = col[i];
+    const int a = ((q / G - ou) % G + G) % G, b = ((q % G - ov) % G + G) % G;
+    const int c = a * kWin + b;
+    val[i] = make_float2(y[2 * c] * sc, y[2 * c + 1] * sc);
+  }
+}
+
+__global__ void k_count_pass(int64_t m, const int8_t *__restrict__ pass, const float *__restrict__ err,
+                             unsigned long long *__restrict__ n, double *__restrict__ esum) {
+  __shared__ double es[256];
+  __shared__ unsigned long long ns[256];
+  double a = 0;
+  unsigned long long c = 0;
+  for (int64_t k = threadIdx.x; k < m; k += blockDim.x) {
+    c += pass[k];
+    a += err[k];
+  }
+  es[threadIdx.x] = a;
+  ns[threadIdx.x] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    unsigned long long u = 0;
+    for (int i = 0; i < 256; ++i) { t += es[i]; u += ns[i]; }
+    *n = u;
+    *esum = t;
+  }
+}
+
 }  // namespace
 
 int64_t mlp_num_params() { return kParams; }
+
+wproj_status build_learned_impl(wproj_plan *p, wproj_mlp *n, const double *uvw, int64_t m, double e, double relmax,
+                                float *row_err, wproj_learned_info *info, cudaStream_t s) {
+  auto t0 = std::chrono::steady_clock::now();
+  WPROJ_TRY(build_kernels_impl(p, uvw, m, e, s));
+  WPROJ_CUDA(cudaStreamSynchronize(s));
+  auto t1 = std::chrono::steady_clock::now();
+  if (p->fmt != WPROJ_INDEX_COLUMNS || p->g.value_dtype != WPROJ_VAL_F32)
+    return fail(WPROJ_ERR_UNSUPPORTED, "build_kernels_learned: needs complex64 values and column indices");
+  const int64_t chunk = 65536;
+  DevBuf x0, Y, err, pass, cnt;
+  WPROJ_TRY(x0.alloc(sizeof(float) * 3 * (m + 128)));
+  WPROJ_TRY(Y.alloc(sizeof(float) * chunk * kOut));
+  WPROJ_TRY(pass.alloc(m));
+  WPROJ_TRY(cnt.alloc(sizeof(double) * 2));
+  float *err_p = row_err;
+  if (!err_p) {
+    WPROJ_TRY(err.alloc(sizeof(float) * m));
+    err_p = err.as<float>();
+  }
+  WPROJ_CUDA(cudaMemsetAsync(x0.ptr, 0, sizeof(float) * 3 * (m + 128), s));
+  k_features<<<ceil_div(m, 256), 256, 0, s>>>(m, uvw, p->g.du, p->g.L, x0.as<float>());
+  WPROJ_CHECK_LAUNCH("mlp features");
+  WPROJ_TRY(ensure_batch(n, chunk));
+  for (int64_t r = 0; r < m; r += chunk) {
+    const int64_t nr = std::min(chunk, m - r);
+    const int64_t B = (nr + 127) / 128 * 128;   // padded rows read zero features
+    WPROJ_TRY(forward(n, x0.as<float>() + 3 * r, B, Y.as<float>(), s));
+    k_judge<<<(unsigned)nr, 256, 0, s>>>(r, uvw, p->row_ptr.as<int64_t>(), p->col.as<int32_t>(), p->val.as<float2>(),
+                                         Y.as<float>(), p->g.G, p->g.du, p->g.W, p->g.beta, e, relmax, err_p,
+                                         pass.as<int8_t>());
+    WPROJ_CHECK_LAUNCH("mlp judge");
+  }
+  WPROJ_TRY(check_err(n, s));
+  WPROJ_TRY(rebuild_cells(p, s));
+  k_count_pass<<<1, 256, 0, s>>>(m, pass.as<int8_t>(), err_p, cnt.as<unsigned long long>(), cnt.as<double>() + 1);
+  WPROJ_CHECK_LAUNCH("mlp pass count");
+  unsigned long long np_ = 0;
+  double es = 0;
+  WPROJ_CUDA(cudaMemcpyAsync(&np_, cnt.ptr, sizeof(np_), cudaMemcpyDeviceToHost, s));
+  WPROJ_CUDA(cudaMemcpyAsync(&es, cnt.as<double>() + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+  WPROJ_CUDA(cudaStreamSynchronize(s));
+  auto t2 = std::chrono::steady_clock::now();
+  p->dr_valid = false;
+  if (info) {
+    info->rows = m;
+    info->learned = int64_t(np_);
+    info->rel_l2_mean = es / double(m);
+    info->plain_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    info->learned_ms = std::chrono::duration<double, std::milli>(t2 - t1).count();
+  }
+  return WPROJ_OK;
+}
 
 wproj_status mlp_create(wproj_mlp *n) {
   WPROJ_TRY(n->P.alloc(sizeof(float) * kParams));
@@ -467,6 +619,15 @@ wproj_status wproj_mlp_gradients(wproj_mlp *n, const float *x0, const float *tva
   if (m < 128 || m % 128 || m > 65536)
     return fail(WPROJ_ERR_INVALID_ARG, "mlp_gradients: m must be a multiple of 128 up to 65536");
   return mlp_gradients(n, x0, tval, tmask, m, mask_weight, loss, grad, static_cast<cudaStream_t>(stream));
+}
+
+wproj_status wproj_build_kernels_learned(wproj_plan *p, wproj_mlp *n, const double *uvw, int64_t m, double e,
+                                         double rel_l2_max, float *row_err, wproj_learned_info *info, void *stream) {
+  if (!p || !n || !uvw) return fail(WPROJ_ERR_INVALID_ARG, "build_kernels_learned: null argument");
+  if (m < 1) return fail(WPROJ_ERR_INVALID_ARG, "build_kernels_learned: m >= 1");
+  if (!(e > 0.0 && e <= 1.0)) return fail(WPROJ_ERR_INVALID_ARG, "build_kernels_learned: e must lie in (0, 1]");
+  if (!(rel_l2_max >= 0.0)) return fail(WPROJ_ERR_INVALID_ARG, "build_kernels_learned: rel_l2_max >= 0");
+  return build_learned_impl(p, n, uvw, m, e, rel_l2_max, row_err, info, static_cast<cudaStream_t>(stream));
 }
 
 wproj_status wproj_mlp_train(wproj_mlp *n, const float *x0, const float *tval, const float *tmask, int64_t m,

@@ -209,6 +209,7 @@ int64_t degrid_partials(const wproj_plan *p);   // partial sums degridding needs
 // cells.cu: cell-major gridding of the column format
 wproj_status build_cells(wproj_plan *p, const int64_t *tptr, const int64_t *cum, int64_t n_seg, cudaStream_t s);
 wproj_status grid_cells(wproj_plan *p, const float2 *y, float2 *Xt2, cudaStream_t s);
+wproj_status rebuild_cells(wproj_plan *p, cudaStream_t s);
 wproj_status batch_grid_cells(const BatchOps &b, const float2 *y, float2 *Xt2, cudaStream_t s);
 
 // gemm.cu: C = A B^T (+ bias) on the tcgen05 tensor cores, BF16 in, FP32 accumulate
@@ -217,6 +218,8 @@ wproj_status gemm_bf16_tn(int M, int N, int K, const __nv_bfloat16 *A, const __n
 
 // mlp.cu: the learned-kernel network
 int64_t mlp_num_params();
+wproj_status build_learned_impl(wproj_plan *p, wproj_mlp *n, const double *uvw, int64_t m, double e, double relmax,
+                                float *row_err, wproj_learned_info *info, cudaStream_t s);
 
 // batches (column format)
 wproj_status batch_degrid(const BatchOps &b, const float2 *Xt, float2 *partial, float2 *y, cudaStream_t s);

@@ -32,7 +32,7 @@ EXPORTED = [
     "wproj_batch_set_schedule", "wproj_batch_phi", "wproj_batch_phi_adj", "wproj_batch_solve_bpdn",
     "wproj_batch_get_info", "wproj_gemm_bf16", "wproj_mlp_num_params", "wproj_mlp_create",
     "wproj_mlp_destroy", "wproj_mlp_set_params", "wproj_mlp_get_params", "wproj_mlp_targets",
-    "wproj_mlp_forward", "wproj_mlp_gradients", "wproj_mlp_train",
+    "wproj_mlp_forward", "wproj_mlp_gradients", "wproj_mlp_train", "wproj_build_kernels_learned",
 ]
 
 
@@ -79,6 +79,11 @@ class BatchInfo(ctypes.Structure):
                 ("nnz", ctypes.c_int64), ("n_pieces", ctypes.c_int64), ("n_chunks", ctypes.c_int64),
                 ("piece", ctypes.c_int64), ("chunk", ctypes.c_int64), ("launches", ctypes.c_int64),
                 ("iter_launches", ctypes.c_int64)]
+
+
+class LearnedInfo(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int64), ("learned", ctypes.c_int64), ("rel_l2_mean", ctypes.c_double),
+                ("plain_ms", ctypes.c_double), ("learned_ms", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -146,6 +151,7 @@ def lib() -> ctypes.CDLL:
         "wproj_mlp_forward": [vp, vp, i64, vp, vp],
         "wproj_mlp_gradients": [vp, vp, vp, vp, i64, dbl, P(dbl), vp, vp],
         "wproj_mlp_train": [vp, vp, vp, vp, i64, i32, i32, dbl, dbl, vp, vp],
+        "wproj_build_kernels_learned": [vp, vp, vp, i64, dbl, dbl, vp, P(LearnedInfo), vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -294,6 +300,20 @@ class Plan:
                                          ctypes.byref(out)))
         self.m = int(out.m)
         return out
+
+    def build_kernels_learned(self, net: "MLP", uvw: torch.Tensor, e: float, rel_l2_max: float = 1e-3,
+                              stream=None):
+        """Plain build, then rows whose predicted kernel passes the checks take it
+        (include/wproj.h).  Returns (info dict, per-row relative L2 errors)."""
+        if uvw.dtype != torch.float64 or uvw.dim() != 2 or uvw.shape[1] != 3:
+            raise WprojError(ERR_INVALID_ARG, "uvw must be an (M, 3) float64 tensor")
+        uvw = uvw.contiguous()
+        err = torch.empty(uvw.shape[0], dtype=torch.float32, device=uvw.device)
+        info = LearnedInfo()
+        _check(lib().wproj_build_kernels_learned(self._h, net._h, _ptr(uvw), uvw.shape[0], float(e),
+                                                 float(rel_l2_max), _ptr(err), ctypes.byref(info), _stream(stream)))
+        self.m = uvw.shape[0]
+        return {f: getattr(info, f) for f, _ in info._fields_}, err
 
     def csr(self) -> CSRView:
         """View of G (see CSRView)."""

@@ -123,3 +123,65 @@ def test_training_reduces_the_loss(wp):
     t = tv[:1024].cpu().numpy()
     assert rel(y1[:, :2048], t) < 0.5 * rel(y0[:, :2048], t)
     net.close()
+
+
+def test_learned_build_judges_every_row(wp):
+    # a briefly trained network; rows take its kernel only when they pass
+    plan, uvw, offs, wc, x0, tv, tm = make_dataset(wp, 8192, 21)
+    plan.close()
+    net = wp.MLP(torch.from_numpy(synth.mlp_init_params(2)))
+    net.train(x0, tv, tm, batch=1024, steps=200, lr=1e-3, mask_weight=0.1)
+    m, N = 1024, 256
+    offs2, wc2 = synth.mlp_samples(m, 31)
+    uvw2 = torch.from_numpy(synth.mlp_uvw(offs2, wc2, N, L, 32)).to(dev())
+    ref = wp.Plan(N, L, box="rule", index_format="columns")
+    ref.build_kernels(uvw2, 0.99)
+    c_ref = ref.csr()
+    # threshold 0: every row falls back, G is the plain one bit for bit
+    p0 = wp.Plan(N, L, box="rule", index_format="columns")
+    info0, err0 = p0.build_kernels_learned(net, uvw2, 0.99, rel_l2_max=0.0)
+    assert info0["learned"] == 0 and info0["rows"] == m
+    assert torch.equal(p0.csr().val, c_ref.val) and torch.equal(p0.csr().col, c_ref.col)
+    # no error threshold: rows whose predicted support holds >= e take the prediction
+    p1 = wp.Plan(N, L, box="rule", index_format="columns")
+    info1, err1 = p1.build_kernels_learned(net, uvw2, 0.99, rel_l2_max=1e9)
+    assert torch.equal(err0, err1) and 0 <= info1["learned"] <= m
+    c1 = p1.csr()
+    assert torch.equal(c1.col, c_ref.col)                      # the support is the plain one
+    changed = (c1.val != c_ref.val).any().item()
+    assert changed == (info1["learned"] > 0)
+    # predicted values on a passing row's support, from the network's own forward
+    xf, _, _ = wp.MLP.targets(ref, uvw2)
+    y = net.forward(xf).cpu().numpy()
+    rp = c_ref.row_ptr.cpu().numpy()
+    beta = O.kb_beta()
+    du_cell = 1.0 / (2.0 * L)
+    checked = 0
+    for k in range(m):
+        col, v1 = c1.rows(k, k + 1)
+        _, v0 = c_ref.rows(k, k + 1)
+        if torch.equal(v1, v0):
+            continue
+        col, v1 = col.cpu().numpy(), v1.cpu().numpy()
+        j0 = np.floor(uvw2[k, :2].cpu().numpy() / du_cell).astype(int)
+        a = (col // (2 * N) - (j0[0] - 16)) % (2 * N)
+        b = (col % (2 * N) - (j0[1] - 16)) % (2 * N)
+        du, dv = offs2[k]
+        ekb = (sum(float(O.kb(du - t, 4, beta)) ** 2 for t in (-1, 0, 1, 2)) *
+               sum(float(O.kb(dv - t, 4, beta)) ** 2 for t in (-1, 0, 1, 2)))
+        cidx = a * 32 + b
+        pred = (y[k, 2 * cidx] + 1j * y[k, 2 * cidx + 1]) * math.sqrt(ekb)
+        assert np.allclose(v1, pred, rtol=1e-5, atol=1e-6 * np.abs(pred).max())
+        checked += 1
+        if checked == 5:
+            break
+    # the operator of the learned G is still self-adjoint-consistent (cells rebuilt)
+    rng = np.random.default_rng(3)
+    x = torch.from_numpy(rng.standard_normal((N, N)).astype(np.float32)).to(dev())
+    yv = torch.from_numpy((rng.standard_normal(m) + 1j * rng.standard_normal(m)).astype(np.complex64)).to(dev())
+    lhs = torch.vdot(yv.to(torch.complex128), p1.phi(x).to(torch.complex128)).real.item()
+    rhs = float((x.double() * p1.phi_adj(yv).double()).sum().item())
+    assert abs(lhs - rhs) <= 1e-4 * abs(lhs)
+    for p in (ref, p0, p1):
+        p.close()
+    net.close()
