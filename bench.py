@@ -52,7 +52,9 @@ def parse():
     ap.add_argument("--value-dtype", default="f32", choices=["f32", "bf16", "f16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-rows", type=int, default=64)
-    ap.add_argument("--workload", default="paper", choices=["paper", "precision", "batched"])
+    ap.add_argument("--workload", default="paper", choices=["paper", "precision", "batched", "learned"])
+    ap.add_argument("--train-kernels", type=int, default=2 ** 20, help="learned workload: training kernels")
+    ap.add_argument("--train-steps", type=int, default=1024, help="learned workload: Adam steps (batch 4096)")
     ap.add_argument("--batch-problems", type=int, default=None, help="problems of the batched workload")
     ap.add_argument("--no-plain", action="store_true", help="batched workload: skip the one-by-one comparison")
     ap.add_argument("--index-format", default="auto", choices=["auto", "columns", "mask"])
@@ -538,12 +540,110 @@ def run_batched(args):
     return 0
 
 
+def run_learned(args):
+    """The learned-kernel form: the network trained on plain-build kernels (w_c ~
+    U[0, 4], offsets U[0,1)^2) on the tensor cores, then the learned build of a
+    2048^2 / M = 2^23 problem judged row by row against the plain build."""
+    import torch
+    from paper_1307_3424_gb300 import wproj
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    wl = synth.LEARNED
+    if args.n or args.m:
+        import dataclasses
+        wl = dataclasses.replace(wl, N=args.n or wl.N, M=args.m or wl.M)
+    L = synth.fov_L()
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
+    flop_fwd = 2.0 * (3 * 256 + 2 * 256 * 256 + 256 * 3072)     # per kernel
+    # ---- training data from the plain build
+    m_t = args.train_kernels
+    offs, wc = synth.mlp_samples(m_t, seed=0)
+    uvw_t = torch.from_numpy(synth.mlp_uvw(offs, wc, wl.N, L, 1)).to(dev)
+    pt = wproj.Plan(wl.N, L, box="rule", index_format="columns")
+    pt.build_kernels(uvw_t, wl.e)
+    x0, tv, tm = wproj.MLP.targets(pt, uvw_t)
+    pt.close()
+    net = wproj.MLP(torch.from_numpy(synth.mlp_init_params(0)))
+    batch = 4096
+    net.train(x0, tv, tm, batch=batch, steps=8, lr=1e-3)          # warm-up
+    net.set_params(torch.from_numpy(synth.mlp_init_params(0)))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = net.train(x0, tv, tm, batch=batch, steps=args.train_steps, lr=1e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    train_tflops = args.train_steps * batch * 3.0 * flop_fwd / t_train / 1e12
+    # ---- inference on the tensor cores (CUDA events)
+    xi = x0[:65536].contiguous()
+    net.forward(xi)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(5):
+        net.forward(xi)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_inf = ev0.elapsed_time(ev1) / 5
+    inf_tflops = 65536 * flop_fwd / (t_inf * 1e-3) / 1e12
+    # held-out quality on the training distribution
+    offs_h, wc_h = synth.mlp_samples(16384, seed=7)
+    uvw_h = torch.from_numpy(synth.mlp_uvw(offs_h, wc_h, wl.N, L, 8)).to(dev)
+    ph = wproj.Plan(wl.N, L, box="rule", index_format="columns")
+    info_h, err_h = ph.build_kernels_learned(net, uvw_h, wl.e, rel_l2_max=1e-3)
+    ph.close()
+    eh = err_h.cpu().numpy()
+    del x0, tv, tm
+    # ---- deployment: plain build vs learned build with row-by-row fallback
+    prob = synth.make_problem(wl, seed=0)
+    uvw = torch.from_numpy(prob.uvw).to(dev)
+    pd = wproj.Plan(wl.N, L, box="rule", index_format="columns")
+    pd.build_kernels(uvw, wl.e)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pd.build_kernels(uvw, wl.e)
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    info, err = pd.build_kernels_learned(net, uvw, wl.e, rel_l2_max=1e-3)
+    e_np = err.cpu().numpy()
+    pd.close()
+    t_learned = (info["plain_ms"] + info["learned_ms"]) * 1e-3
+    line = {
+        "metric": "learned_w_kernels_per_s", "value": wl.M / t_learned, "unit": "w-kernels/s", "n_gpus": 1,
+        "steps": args.train_steps, "warmup": 8, "ms_per_step": t_train / args.train_steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": wl.name, "N": wl.N, "G": 2 * wl.N, "M": wl.M, "e": wl.e, "w_c": "U[0, 4]",
+                   "box": "rule S(w)", "network": "3-256-256-256-3072 GELU, BF16 GEMMs (tcgen05), FP32 Adam",
+                   "train_kernels": m_t, "train_batch": batch, "train_steps": args.train_steps,
+                   "judge": "rel. L2 <= 1e-3 over the 32x32 window and predicted support >= e of the energy"},
+        "plain_build_w_kernels_per_s": wl.M / t_plain,
+        "learned": {"rows": info["rows"], "taken": info["learned"], "fraction": info["learned"] / info["rows"],
+                    "rel_l2_mean": info["rel_l2_mean"], "rel_l2_median": float(np.median(e_np)),
+                    "rel_l2_p10": float(np.percentile(e_np, 10)), "plain_ms": info["plain_ms"],
+                    "infer_and_judge_ms": info["learned_ms"]},
+        "held_out": {"rows": 16384, "rel_l2_median": float(np.median(eh)), "rel_l2_p10": float(np.percentile(eh, 10)),
+                     "fraction_below_1e-2": float(np.mean(eh < 1e-2)), "fraction_below_1e-3": float(np.mean(eh < 1e-3))},
+        "training": {"seconds": t_train, "samples_per_s": args.train_steps * batch / t_train,
+                     "tflops": train_tflops, "loss_first": losses[0], "loss_last": float(np.mean(losses[-16:]))},
+        "roofline": {"kernel": "k_gemm_tn (MLP forward, 65536 kernels)", "bound": "tensor",
+                     "achieved": inf_tflops, "peak": bf16_peak, "unit": "TFLOP/s", "frac": inf_tflops / bf16_peak,
+                     "traffic": None, "peak_source": "measured (cuBLAS bf16 burst)", "ms": t_inf},
+    }
+    print(json.dumps(line))
+    net.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "learned":
+        return run_learned(args)
     res = run_ours(args)
     out, kst = res
     if out is not None:

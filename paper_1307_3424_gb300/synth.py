@@ -185,6 +185,12 @@ def random_uvw(rng: np.random.Generator, M: int, N: int, L: float,
     return np.ascontiguousarray(np.concatenate([uv, w[:, None]], axis=1))
 
 
+# The learned-kernel deployment: 2048x2048 (8000 blobs plus the power-law part),
+# M = 2^23, w_c ~ U[0, 4] cells, box rule S(w).
+LEARNED = Workload("blobs2048_m8388608", N=2048, n_blobs=8000, M=2 ** 23, uv="uniform",
+                   wd_max=4.0, e=0.99, dr_iters=50, powerlaw=True, w_unit="cells", box="rule")
+
+
 # The batched form: many independent problems of uneven size.  Image sides are
 # drawn log-uniformly from the powers of two 64 .. 512 (the FFTs are radix 2/4),
 # M = f N^2 with f ~ U[0.1, 1], a per-problem w_c,max ~ U[0, 2] cells with
