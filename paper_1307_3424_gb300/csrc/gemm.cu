@@ -9,9 +9,12 @@
 // matrices 128 B apart, row-adjacent ones 1 KB apart), one thread issues four
 // tcgen05.mma (K = 16 each) accumulating into a 128 x 128 FP32 tile in tensor
 // memory, and tcgen05.commit signals an mbarrier when they have read the
-// slice.  Two slices are staged, so the copy of slice k+1 overlaps the MMAs of
-// slice k.  The epilogue reads the accumulator with tcgen05.ld (warp w owns
-// TMEM lanes 32w..32w+31 = rows of C), adds the bias and stores.
+// slice.  Slices are copied with cp.async, two in flight per CTA and three
+// CTAs per SM; a stage is refilled once the MMAs that
+// read it have completed.  The epilogue reads the accumulator with tcgen05.ld
+// (warp w owns TMEM lanes 32w..32w+31 = rows of C), transposes each 32 x 32
+// block through shared memory so that stores are row-contiguous, adds the bias
+// and stores.
 //
 // Shapes: M, N multiples of 128, K a multiple of 64 (the callers pad).  Waits
 // are bounded; a wait that runs out sets *err, and the CTA still frees its
@@ -25,7 +28,7 @@ namespace {
 constexpr int kBM = 128, kBN = 128, kBK = 64;
 constexpr int kSliceA = kBM * kBK * 2;   // bytes of one A slice (16 KB)
 constexpr int kSliceB = kBN * kBK * 2;
-constexpr int kStages = 2;
+constexpr int kStages = 2;   // slices in flight (3 CTAs fit on an SM)
 constexpr unsigned long long kGemmWaitNs = 2000000000ull;
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
@@ -74,15 +77,21 @@ __host__ __device__ constexpr uint32_t instr_desc(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
 }
 
-// copy a rows x 64 bf16 slice (row stride ld elements) into the core-matrix layout
+// asynchronous copy (cp.async, 16 B per request) of a rows x 64 bf16 slice
+// (row stride ld elements) into the core-matrix layout
 __device__ __forceinline__ void stage_slice(const __nv_bfloat16 *__restrict__ g, int64_t ld, int rows,
                                             unsigned char *s) {
   for (int i = threadIdx.x; i < rows * 8; i += blockDim.x) {
     const int r = i >> 3, c = i & 7;   // row, 16-byte chunk along K
-    const uint4 v = __ldg(reinterpret_cast<const uint4 *>(g + int64_t(r) * ld) + c);
-    *reinterpret_cast<uint4 *>(s + ((r >> 3) * 8 + c) * 128 + (r & 7) * 16) = v;
+    const void *src = reinterpret_cast<const uint4 *>(g + int64_t(r) * ld) + c;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(s + ((r >> 3) * 8 + c) * 128 + (r & 7) * 16)),
+                 "l"(src)
+                 : "memory");
   }
 }
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 template <bool OUT_BF16>
 __global__ void __launch_bounds__(128)
@@ -113,14 +122,19 @@ k_gemm_tn(int M, int N, int K, const __nv_bfloat16 *__restrict__ A, const __nv_b
   const uint32_t idesc = instr_desc(kBM, kBN);
   const int nk = K / kBK;
   bool ok = true;
+  // every thread commits one copy group per slice (empty past the end), so
+  // slice k's group is complete once at most kStages - 1 younger groups pend
+  for (int k = 0; k < kStages; ++k) {
+    if (k < nk) {
+      stage_slice(A + int64_t(m0) * K + int64_t(k) * kBK, K, kBM, sa + k * kSliceA);
+      stage_slice(B + int64_t(n0) * K + int64_t(k) * kBK, K, kBN, sb + k * kSliceB);
+    }
+    cp_commit();
+  }
   for (int k = 0; k < nk && ok; ++k) {
     const int st = k % kStages;
-    // the MMAs that last read this stage (slice k - kStages) must be done
-    if (k >= kStages) ok = __syncthreads_and(mbar_wait_bounded(&done[st], ((k / kStages) - 1) & 1));
-    if (!ok) break;
-    stage_slice(A + int64_t(m0) * K + int64_t(k) * kBK, K, kBM, sa + st * kSliceA);
-    stage_slice(B + int64_t(n0) * K + int64_t(k) * kBK, K, kBN, sb + st * kSliceB);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic stores -> async proxy
+    cp_wait<kStages - 1>();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // copies -> async proxy (tcgen05)
     __syncthreads();
     if (threadIdx.x == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -141,17 +155,26 @@ k_gemm_tn(int M, int N, int K, const __nv_bfloat16 *__restrict__ A, const __nv_b
                        su32(&done[st]))
                    : "memory");
     }
+    // refill this stage with slice k + kStages once its MMAs have read it
+    const int nx = k + kStages;
+    if (nx < nk) {
+      ok = __syncthreads_and(mbar_wait_bounded(&done[st], (k / kStages) & 1));
+      if (ok) {
+        stage_slice(A + int64_t(m0) * K + int64_t(nx) * kBK, K, kBM, sa + st * kSliceA);
+        stage_slice(B + int64_t(n0) * K + int64_t(nx) * kBK, K, kBN, sb + st * kSliceB);
+      }
+    }
+    cp_commit();
   }
+  cp_wait<0>();
   // all MMAs done: the last commit of each stage in use
-  if (ok && nk > 0) {
+  if (ok && nk > 0) {   // the last commit covers every earlier MMA
     const int kl = nk - 1;
     ok = __syncthreads_and(mbar_wait_bounded(&done[kl % kStages], (kl / kStages) & 1));
-    if (ok && nk > 1) ok = __syncthreads_and(mbar_wait_bounded(&done[(kl - 1) % kStages], ((kl - 1) / kStages) & 1));
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (ok) {
     // warp w reads TMEM lanes 32w.. (rows m0 + 32w + lane), 32 columns at a time
-    const int row = m0 + warp * 32 + lane;
 #pragma unroll 1
     for (int c0 = 0; c0 < kBN; c0 += 32) {
       uint32_t r[32];
@@ -167,15 +190,24 @@ k_gemm_tn(int M, int N, int K, const __nv_bfloat16 *__restrict__ A, const __nv_b
           : "r"(taddr)
           : "memory");
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (row < M) {
+      // transpose the warp's 32 x 32 block through shared memory (the staging
+      // area is free now), so that each store instruction writes one row
+      float *blk = reinterpret_cast<float *>(smem) + warp * 32 * 33;
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const int col = n0 + c0 + i;
-          float v = __uint_as_float(r[i]) + (bias ? __ldg(bias + col) : 0.f);
-          if (OUT_BF16) reinterpret_cast<__nv_bfloat16 *>(C)[int64_t(row) * N + col] = __float2bfloat16_rn(v);
-          else reinterpret_cast<float *>(C)[int64_t(row) * N + col] = v;
+      for (int i = 0; i < 32; ++i) blk[lane * 33 + i] = __uint_as_float(r[i]);
+      __syncwarp();
+      const int col = n0 + c0 + lane;
+      const float bv = bias ? __ldg(bias + col) : 0.f;
+#pragma unroll 4
+      for (int i = 0; i < 32; ++i) {
+        const int rr = m0 + warp * 32 + i;
+        const float v = blk[i * 33 + lane] + bv;
+        if (rr < M) {
+          if (OUT_BF16) reinterpret_cast<__nv_bfloat16 *>(C)[int64_t(rr) * N + col] = __float2bfloat16_rn(v);
+          else reinterpret_cast<float *>(C)[int64_t(rr) * N + col] = v;
         }
       }
+      __syncwarp();
     }
   } else if (threadIdx.x == 0) {
     atomicOr(err, 1);

@@ -38,6 +38,8 @@ struct wproj_mlp {
   int64_t step = 0;
   int64_t cap = 0;                      // batch capacity of the activation buffers
   wproj::DevBuf Z1, Z2, Z3, H1, H2, H3, Y, dY, dYt, Ht, dZt, dH, dZ, dZ1, part, err;
+  wproj::DevBuf csum;                   // column-sum partials and the first layer's sums
+  int64_t csum_off = 0;
 };
 
 namespace wproj {
@@ -115,14 +117,53 @@ __global__ void k_transpose(int64_t R, int64_t C, const __nv_bfloat16 *__restric
     if (c0 + i < C && r0 + threadIdx.x < R) out[(c0 + i) * R + r0 + threadIdx.x] = t[threadIdx.x][i];
 }
 
-// out[j] = sum_r in[r][j] in row order (bias gradients)
-template <class T>
-__global__ void k_colsum(int64_t R, int C, const T *__restrict__ in, float *__restrict__ out) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= C) return;
-  float s = 0.f;
-  for (int64_t r = 0; r < R; ++r) s += float(in[r * C + j]);
-  out[j] = s;
+// Column sums in two passes with a fixed order: block (32 columns x 8 row
+// groups) over rows [1024 y, 1024 (y + 1)) -> part[y][NV][col]; then k_sum_chunks.
+// NV = 1: sum_r in[r][j]; NV = 4 (first layer): sum_r in[r][j] (x0[r][0..2], 1).
+constexpr int kChunkRows = 1024;
+template <class T, int NV>
+__global__ void __launch_bounds__(256)
+k_colsum_part(int64_t R, int C, const T *__restrict__ in, const float *__restrict__ x0, float *__restrict__ part) {
+  __shared__ float red[8][NV][32];
+  const int j = blockIdx.x * 32 + threadIdx.x, g = threadIdx.y;
+  const int64_t r0 = int64_t(blockIdx.y) * kChunkRows;
+  const int64_t r1 = r0 + kChunkRows < R ? r0 + kChunkRows : R;
+  float acc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = 0.f;
+  if (j < C) {
+    for (int64_t r = r0 + g; r < r1; r += 8) {
+      const float d = float(in[r * C + j]);
+      if constexpr (NV == 1) {
+        acc[0] += d;
+      } else {
+        acc[0] += d * x0[r * 3];
+        acc[1] += d * x0[r * 3 + 1];
+        acc[2] += d * x0[r * 3 + 2];
+        acc[3] += d;
+      }
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) red[g][v][threadIdx.x] = acc[v];
+  __syncthreads();
+  if (g == 0 && j < C) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      float t = 0.f;
+      for (int q = 0; q < 8; ++q) t += red[q][v][threadIdx.x];
+      part[(int64_t(blockIdx.y) * NV + v) * C + j] = t;
+    }
+  }
+}
+
+// out[v][j] = sum over chunks of part[chunk][v][j], chunks in order
+__global__ void k_sum_chunks(int nchunk, int nv, int C, const float *__restrict__ part, float *__restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nv * C) return;
+  float t = 0.f;
+  for (int c = 0; c < nchunk; ++c) t += part[int64_t(c) * nv * C + i];
+  out[i] = t;
 }
 
 // dZ = dH * GELU'(Z) as BF16 (next GEMM) and, when dZf is given, FP32
@@ -135,22 +176,14 @@ __global__ void k_gelu_bwd(int64_t n, const float *__restrict__ dH, const float 
   }
 }
 
-// first layer gradients: thread j sums over the batch in row order
-__global__ void k_in_bwd(int64_t B, const float *__restrict__ dZ1, const float *__restrict__ x0, float *__restrict__ G) {
+// first layer gradients from out[v][j] of the 4-way column sums
+__global__ void k_in_grad(const float *__restrict__ s4, float *__restrict__ G) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= kH) return;
-  float g0 = 0.f, g1 = 0.f, g2 = 0.f, gb = 0.f;
-  for (int64_t b = 0; b < B; ++b) {
-    const float d = dZ1[b * kH + j];
-    g0 += d * x0[b * 3];
-    g1 += d * x0[b * 3 + 1];
-    g2 += d * x0[b * 3 + 2];
-    gb += d;
-  }
-  G[oW1 + j * kIn] = g0;
-  G[oW1 + j * kIn + 1] = g1;
-  G[oW1 + j * kIn + 2] = g2;
-  G[oB1 + j] = gb;
+  G[oW1 + j * kIn] = s4[j];
+  G[oW1 + j * kIn + 1] = s4[kH + j];
+  G[oW1 + j * kIn + 2] = s4[2 * kH + j];
+  G[oB1 + j] = s4[3 * kH + j];
 }
 
 __global__ void k_adam(int64_t n, float *__restrict__ P, const float *__restrict__ G, float *__restrict__ M,
@@ -172,6 +205,16 @@ __global__ void k_to_bf16(int64_t n, const float *__restrict__ in, __nv_bfloat16
 }
 
 int blocks_for(int64_t n) { return (int)std::min<int64_t>(152 * 16, std::max<int64_t>(1, ceil_div(n, 256))); }
+
+// column sums of an R x C matrix (NV = 1), or the first layer's four (NV = 4)
+template <class T, int NV>
+wproj_status colsum(int64_t R, int C, const T *in, const float *x0, float *scratch, float *out, cudaStream_t s) {
+  const int nchunk = ceil_div(R, kChunkRows);
+  k_colsum_part<T, NV><<<dim3(ceil_div(C, 32), nchunk), dim3(32, 8), 0, s>>>(R, C, in, x0, scratch);
+  k_sum_chunks<<<ceil_div(NV * C, 256), 256, 0, s>>>(nchunk, NV, C, scratch, out);
+  WPROJ_CHECK_LAUNCH("column sums");
+  return WPROJ_OK;
+}
 
 wproj_status transpose(int64_t R, int64_t C, const __nv_bfloat16 *in, __nv_bfloat16 *out, cudaStream_t s) {
   k_transpose<<<dim3(ceil_div(C, 32), ceil_div(R, 32)), dim3(32, 8), 0, s>>>(R, C, in, out);
@@ -208,6 +251,9 @@ wproj_status ensure_batch(wproj_mlp *n, int64_t B) {
   WPROJ_TRY(n->dH.alloc(sizeof(float) * B * kH));
   WPROJ_TRY(n->dZ.alloc(2 * B * kH));
   WPROJ_TRY(n->dZ1.alloc(sizeof(float) * B * kH));
+  // column-sum partials: up to ceil(B / 1024) chunks x max(3072, 4 x 256) columns, then 4 x 256 results
+  n->csum_off = int64_t(ceil_div(B, kChunkRows)) * kOut;
+  WPROJ_TRY(n->csum.alloc(sizeof(float) * (n->csum_off + 4 * kH)));
   n->cap = B;
   return WPROJ_OK;
 }
@@ -245,7 +291,7 @@ wproj_status backward(wproj_mlp *n, const float *x0, const float *Tv, const floa
   WPROJ_TRY(transpose(B, kOut, n->dY.as<__nv_bfloat16>(), n->dYt.as<__nv_bfloat16>(), s));
   WPROJ_TRY(transpose(B, kH, H[2], n->Ht.as<__nv_bfloat16>(), s));
   WPROJ_TRY(gemm(kOut, kH, (int)B, n->dYt.ptr, n->Ht.ptr, nullptr, G + oW4, n, s));
-  k_colsum<__nv_bfloat16><<<ceil_div(kOut, 256), 256, 0, s>>>(B, kOut, n->dY.as<__nv_bfloat16>(), G + oB4);
+  WPROJ_TRY((colsum<__nv_bfloat16, 1>(B, kOut, n->dY.as<__nv_bfloat16>(), nullptr, n->csum.as<float>(), G + oB4, s)));
   WPROJ_TRY(gemm((int)B, kH, kOut, n->dY.ptr, n->W4t.ptr, nullptr, n->dH.ptr, n, s));
   // layers 3 and 2
   const __nv_bfloat16 *Wt[2] = {n->W3t.as<__nv_bfloat16>(), n->W2t.as<__nv_bfloat16>()};
@@ -257,12 +303,13 @@ wproj_status backward(wproj_mlp *n, const float *x0, const float *Tv, const floa
     WPROJ_TRY(transpose(B, kH, n->dZ.as<__nv_bfloat16>(), n->dZt.as<__nv_bfloat16>(), s));
     WPROJ_TRY(transpose(B, kH, H[zi - 1], n->Ht.as<__nv_bfloat16>(), s));
     WPROJ_TRY(gemm(kH, kH, (int)B, n->dZt.ptr, n->Ht.ptr, nullptr, G + oW[l], n, s));
-    k_colsum<__nv_bfloat16><<<1, kH, 0, s>>>(B, kH, n->dZ.as<__nv_bfloat16>(), G + oB[l]);
+    WPROJ_TRY((colsum<__nv_bfloat16, 1>(B, kH, n->dZ.as<__nv_bfloat16>(), nullptr, n->csum.as<float>(), G + oB[l], s)));
     WPROJ_TRY(gemm((int)B, kH, kH, n->dZ.ptr, Wt[l], nullptr, n->dH.ptr, n, s));
   }
   // layer 1
   k_gelu_bwd<<<blocks_for(B * kH), 256, 0, s>>>(B * kH, n->dH.as<float>(), Z[0], nullptr, n->dZ1.as<float>());
-  k_in_bwd<<<1, kH, 0, s>>>(B, n->dZ1.as<float>(), x0, G);
+  WPROJ_TRY((colsum<float, 4>(B, kH, n->dZ1.as<float>(), x0, n->csum.as<float>(), n->csum.as<float>() + n->csum_off, s)));
+  k_in_grad<<<1, kH, 0, s>>>(n->csum.as<float>() + n->csum_off, G);
   WPROJ_CHECK_LAUNCH("mlp layer 1 backward");
   return WPROJ_OK;
 }
