@@ -383,6 +383,85 @@ def phi_adj(geo: Geometry, Gm, y):
     return AZ_adj(geo, F_adj(geo, Xt))
 
 
+# ----------------------------------------------------------------------------
+# Paper mode: the paper's own operator Phi' = C-hat F U of Section 2.2 (Eq. 8)
+# for visibilities on the grid: U upsamples the N x N image by zero-padding its
+# spectrum to the 2N x 2N grid, C-hat's row k is the Fourier transform of the
+# chirp on the upsampled image (Eq. 5, linear), centred on the visibility's
+# grid cell.  The grid cell is 1/L (the upsampled image spans the field of view
+# L with 2N pixels of L/2N), so the kernel rows are those of `kernel_box` for a
+# geometry with field of view L/2, one gridding tap and S = G.
+# ----------------------------------------------------------------------------
+
+
+def paper_geometry(N: int, L: float, chirp_kind: str = "linear") -> Geometry:
+    """Kernel geometry of paper mode: the chirp sampled on the upsampled image
+    (offsets (P - G/2) L/G), grid cells 1/L, delta gridding."""
+    return Geometry(N, L / 2.0, W=1, chirp_kind=chirp_kind)
+
+
+def _natural(x):
+    """Image with pixel offset p - N/2 moved to index (p - N/2) mod N."""
+    N = x.shape[0]
+    return np.roll(np.asarray(x), (-(N // 2), -(N // 2)), axis=(0, 1))
+
+
+def paper_spectrum(x, G: int):
+    """P F_N x: the unitary spectrum of the N x N image (natural order) placed
+    on the G x G grid (frequency k in [-N/2, N/2) at index k mod G), zeros
+    elsewhere.  F_G U x equals this for U = F_G^H P F_N (U is an isometry)."""
+    N = x.shape[0]
+    XN = np.fft.fft2(_natural(x)) / N
+    k = np.arange(-(N // 2), N // 2)
+    X = np.zeros((G, G), dtype=np.complex128)
+    X[np.ix_(k % G, k % G)] = XN[np.ix_(k % N, k % N)]
+    return X
+
+
+def paper_spectrum_adj(X, N: int):
+    """(P F_N)^H X: crop the [-N/2, N/2)^2 block, inverse unitary DFT, back to
+    pixel order."""
+    G = X.shape[0]
+    k = np.arange(-(N // 2), N // 2)
+    XN = np.zeros((N, N), dtype=np.complex128)
+    XN[np.ix_(k % N, k % N)] = X[np.ix_(k % G, k % G)]
+    xn = np.fft.ifft2(XN) * N
+    return np.roll(xn, (N // 2, N // 2), axis=(0, 1))
+
+
+def paper_upsample(x, G: int):
+    """U x = F_G^H P F_N x in natural order (offset o at index o mod G)."""
+    return np.fft.ifft2(paper_spectrum(x, G)) * G
+
+
+def paper_phi(N: int, Gm, x):
+    """Phi' x = C-hat F U x = C-hat P F_N x."""
+    return Gm @ paper_spectrum(np.asarray(x, dtype=np.float64), 2 * N).ravel()
+
+
+def paper_phi_adj(N: int, Gm, y):
+    Xt = np.conj(Gm.T @ np.conj(np.asarray(y))).reshape(2 * N, 2 * N)
+    return paper_spectrum_adj(Xt, N)
+
+
+def paper_visibilities_direct(N: int, L: float, x, uvw, chirp_kind: str = "linear"):
+    """The definition itself, for pins: y_k = [F_G (c_k . U x)] at the grid
+    cell (u_k L, v_k L) mod G, with c_k the chirp on the upsampled image's
+    pixels (offset o at l = o L / G, natural order) and F_G unitary."""
+    G = 2 * N
+    ux = paper_upsample(np.asarray(x, dtype=np.float64), G)
+    o = np.arange(G)
+    o = np.where(o < G // 2, o, o - G)
+    l = o * (L / G)
+    y = np.empty(uvw.shape[0], dtype=np.complex128)
+    for k in range(uvw.shape[0]):
+        u, v, w = uvw[k]
+        c = chirp(l[:, None], l[None, :], w, chirp_kind)
+        Y = np.fft.fft2(c * ux) / G
+        y[k] = Y[int(math.floor(u * L)) % G, int(math.floor(v * L)) % G]
+    return y
+
+
 def visibilities_direct(geo: Geometry, x, uvw):
     """Brute-force discretisation of Eq. 1 (Eq. 3 with the chirp of Eq. 4)
     as a pixel sum, with the 1/G factor of the unitary F:

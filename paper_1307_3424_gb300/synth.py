@@ -266,3 +266,24 @@ def mlp_uvw(offsets: np.ndarray, wc: np.ndarray, N: int, L: float, seed: int = 1
     uv = (cells + offsets) * du
     w = 2.0 * wc / (L * L)
     return np.ascontiguousarray(np.concatenate([uv, w[:, None]], axis=1))
+
+
+def paper_problem(N: int, coverage: float, seed: int = 0, wd: float | None = None, n_blobs: int = 20,
+                  L: float | None = None) -> Problem:
+    """The paper's own set-up (Section 4.1): visibilities on the 2N x 2N grid
+    (cells 1/L), a fraction `coverage` of all grid cells drawn uniformly
+    without replacement, w_d ~ U[0, 1] (or the constant `wd`), w = w_d N / L^2.
+    (u, v) = (j + 1e-9) / L for grid cell j in [-N, N), so that floor(u L) = j
+    exactly.  Order: sky -> cells -> w (noise: draw_noise)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    L = fov_L() if L is None else L
+    G = 2 * N
+    x = blob_sky(rng, N, n_blobs)
+    M = max(1, int(round(coverage * G * G)))
+    flat = rng.choice(G * G, M, replace=False)
+    cells = np.stack([flat // G - N, flat % G - N], axis=1).astype(np.float64)
+    wdv = rng.uniform(0.0, 1.0, M) if wd is None else np.full(M, float(wd))
+    w = wdv * N / (L * L)
+    uvw = np.ascontiguousarray(np.concatenate([(cells + 1e-9) / L, w[:, None]], axis=1))
+    wl = Workload(f"paper{N}_cov{coverage}", N=N, n_blobs=n_blobs, M=M, uv="grid", wd_max=1.0, e=0.75)
+    return Problem(wl, L, x, uvw, wdv, rng)
