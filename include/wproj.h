@@ -78,6 +78,13 @@ typedef struct {
   int32_t value_dtype;  /* wproj_value_dtype of the stored G values; bf16/f16 values are
                            scaled per row by 1 / max|G[k,:]| (row_scale holds max|G[k,:]|) */
   int32_t index_format; /* wproj_index_format: how the columns of G are stored */
+  int32_t upsampling;   /* 0: the model above (image-space zero-padding Z, KB correction A,
+                           grid cells 1/(2L)).  1: the paper's own operator (Section 2.2,
+                           Eq. 8): Phi = C-hat F U with U the upsampling that zero-pads the
+                           image's spectrum onto the 2N x 2N grid (an isometry), the chirp
+                           sampled on the upsampled image (2N pixels of L/2N), grid cells
+                           1/L, (u, v) in [-N/L, N/L); needs kb_support = 1 (visibilities
+                           on the grid: the cell is floor(u L)) and n >= 16 */
 } wproj_grid_desc;
 
 /* Storage of G.  The entries of a row are grouped by 32 x 32 grid tile (tiles
@@ -135,6 +142,11 @@ typedef struct {
   int32_t resume;       /* 1: continue from the plan's current DR state (z, u, gamma,
                            ||Phi||^2) left by the previous solve or wproj_dr_state_set;
                            0: start from z = Re Phi^H y, u = 0 */
+  int32_t psi;          /* sparsity basis Psi of Eq. 7: 0 = Dirac (x itself is sparse),
+                           p in 1..WPROJ_DAUB_MAX_P = periodic orthonormal Daubechies
+                           wavelets with p vanishing moments (8: the paper's Db8) */
+  int32_t psi_levels;   /* dyadic levels of the wavelet transform (N divisible by
+                           2^levels); ignored for psi = 0 */
 } wproj_dr_params;
 
 typedef struct {
@@ -218,11 +230,16 @@ wproj_status wproj_phi_cplx(wproj_plan *p, const void *x_cplx, void *y, void *st
 
 /* ---- Part III: BPDN by Douglas-Rachford (Eq. 7) --------------------------- */
 
-/* Solve min ||x||_1 s.t. ||y - Phi x||_2 <= eps over real x.  y: device M
+/* Solve min ||alpha||_1 s.t. ||y - Phi Psi alpha||_2 <= eps over real alpha and
+ * return the image x = Psi alpha (Psi = identity for psi = 0).  y: device M
  * float2; x_out: device N x N float32.  prm NULL = defaults (T = 50, 10 inner
- * iterations, gamma_frac 1e-2, lambda 1, power iteration 100).  info (nullable)
- * makes the call synchronous and fills the summary; with info NULL the call is
- * asynchronous. */
+ * iterations, gamma_frac 1e-2, lambda 1, power iteration 100, Dirac basis).
+ * info (nullable) makes the call synchronous and fills the summary (final_l1 =
+ * ||alpha||_1); with info NULL the call is asynchronous.
+ * With a wavelet Psi the DR variable z lives in coefficient space and the
+ * projection onto {alpha : ||y - Phi Psi alpha|| <= eps} is taken in image space
+ * as Psi^T P(Psi z), which is exact because Psi is orthonormal: one synthesis
+ * and one analysis per outer iteration, none inside the inner loop. */
 wproj_status wproj_solve_bpdn(wproj_plan *p, const void *y, double eps,
                               const wproj_dr_params *prm, float *x_out,
                               wproj_solve_info *info, void *stream);
@@ -231,7 +248,8 @@ wproj_status wproj_solve_bpdn(wproj_plan *p, const void *y, double eps,
  * constant image 1/N (synchronous). */
 wproj_status wproj_power_norm2(wproj_plan *p, int32_t iters, double *out, void *stream);
 
-/* Checkpoint / resume of the Douglas-Rachford state: z (N x N float32), the dual
+/* Checkpoint / resume of the Douglas-Rachford state: z (N x N float32; wavelet
+ * coefficients when the solve used a wavelet Psi, which resume must use again), the dual
  * variable u (M float2, one per visibility of the current G), gamma and ||Phi||^2.
  * Pointers may be host or device memory (copied with cudaMemcpyDefault, then the
  * stream is synchronised).  get needs a previous solve (WPROJ_ERR_NOT_BUILT
@@ -248,6 +266,25 @@ wproj_status wproj_dr_state_set(wproj_plan *p, const float *z, const void *u, do
  * 16 <= n <= 4096): out[k] = sum_j in[j] exp(sign 2 pi i k.j / n), sign -1
  * (inverse = 0) or +1 (inverse = 1).  in and out: device float2, may alias. */
 wproj_status wproj_fft2d(const void *in, void *out, int32_t n, int32_t batch, int32_t inverse,
+                         void *stream);
+
+/* The Daubechies sparsity basis (Eq. 7; Db8 in the paper's experiments).
+ * Taps: the low-pass analysis filter of the extremal-phase Daubechies wavelet with
+ * p vanishing moments (1 <= p <= WPROJ_DAUB_MAX_P), 2p doubles into h_out (host),
+ * from Daubechies' spectral factorisation; the high-pass is g_k = (-1)^k h_{2p-1-k}.
+ * One periodic level on an even length n: a_i = sum_k h_k x_{(2i+k) mod n},
+ * d_i = sum_k g_k x_{(2i+k) mod n}.  In 2-D a level filters the fast axis, then
+ * the slow axis, and stores the Mallat layout: [0,h)x[0,h) low-low, [0,h)x[h,n)
+ * low (slow) / high (fast), [h,n)x[0,h) high / low, [h,n)x[h,n) high-high; the
+ * next level transforms the low-low block.
+ * wproj_dwt2: alpha = Psi^T x; wproj_idwt2: x = Psi alpha.  x, alpha: device
+ * n x n float32, row-major, must not alias; work: device scratch of n*n/2
+ * floats; n divisible by 2^levels, levels >= 1.  Asynchronous on `stream`. */
+#define WPROJ_DAUB_MAX_P 10
+wproj_status wproj_daubechies_taps(int32_t p, double *h_out);
+wproj_status wproj_dwt2(int32_t n, int32_t levels, int32_t p, const float *x, float *alpha, float *work,
+                        void *stream);
+wproj_status wproj_idwt2(int32_t n, int32_t levels, int32_t p, const float *alpha, float *x, float *work,
                          void *stream);
 
 /* Per-kernel device timing with CUDA events (0 = off, default). */

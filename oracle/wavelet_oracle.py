@@ -72,54 +72,51 @@ def highpass_taps(h: np.ndarray) -> np.ndarray:
     return np.array([(-1.0) ** k * h[L - 1 - k] for k in range(L)])
 
 
-def dwt1(x: np.ndarray, h: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
-    """One periodic analysis level of a 1-D signal of even length n."""
-    n = x.size
+def dwt1(x: np.ndarray, h: np.ndarray, axis: int = -1) -> tuple[np.ndarray, np.ndarray]:
+    """One periodic analysis level along `axis` (even length n):
+    a_i = sum_k h_k x_{(2i + k) mod n}, d_i = sum_k g_k x_{(2i + k) mod n}."""
+    x = np.moveaxis(np.asarray(x), axis, -1)
+    n = x.shape[-1]
     g = highpass_taps(h)
-    a = np.zeros(n // 2, dtype=np.result_type(x, h))
-    d = np.zeros(n // 2, dtype=np.result_type(x, h))
-    for i in range(n // 2):
-        for k in range(h.size):
-            a[i] += h[k] * x[(2 * i + k) % n]
-            d[i] += g[k] * x[(2 * i + k) % n]
-    return a, d
+    i = np.arange(n // 2)
+    a = np.zeros(x.shape[:-1] + (n // 2,), dtype=np.result_type(x, h))
+    d = np.zeros_like(a)
+    for k in range(h.size):
+        xs = x[..., (2 * i + k) % n]
+        a += h[k] * xs
+        d += g[k] * xs
+    return np.moveaxis(a, -1, axis), np.moveaxis(d, -1, axis)
 
 
-def idwt1(a: np.ndarray, d: np.ndarray, h: np.ndarray) -> np.ndarray:
+def idwt1(a: np.ndarray, d: np.ndarray, h: np.ndarray, axis: int = -1) -> np.ndarray:
     """Transpose of dwt1: x_j = sum_{i,k : (2i + k) mod n = j} (h_k a_i + g_k d_i)."""
-    n = 2 * a.size
+    a = np.moveaxis(np.asarray(a), axis, -1)
+    d = np.moveaxis(np.asarray(d), axis, -1)
+    n = 2 * a.shape[-1]
     g = highpass_taps(h)
-    x = np.zeros(n, dtype=np.result_type(a, h))
-    for i in range(n // 2):
-        for k in range(h.size):
-            x[(2 * i + k) % n] += h[k] * a[i] + g[k] * d[i]
-    return x
+    i = np.arange(n // 2)
+    x = np.zeros(a.shape[:-1] + (n,), dtype=np.result_type(a, h))
+    for k in range(h.size):
+        # the positions (2i + k) mod n are distinct over i for a fixed k
+        x[..., (2 * i + k) % n] += h[k] * a + g[k] * d
+    return np.moveaxis(x, -1, axis)
 
 
 def _level_2d(block: np.ndarray, h: np.ndarray) -> np.ndarray:
     n = block.shape[0]
     hh = n // 2
-    tmp = np.empty_like(block)
-    for r in range(n):                       # fast axis
-        a, d = dwt1(block[r], h)
-        tmp[r, :hh], tmp[r, hh:] = a, d
+    lo, hi = dwt1(block, h, axis=1)          # fast axis
     out = np.empty_like(block)
-    for c in range(n):                       # slow axis
-        a, d = dwt1(tmp[:, c], h)
-        out[:hh, c], out[hh:, c] = a, d
+    out[:hh, :hh], out[hh:, :hh] = dwt1(lo, h, axis=0)     # slow axis
+    out[:hh, hh:], out[hh:, hh:] = dwt1(hi, h, axis=0)
     return out
 
 
 def _ilevel_2d(block: np.ndarray, h: np.ndarray) -> np.ndarray:
-    n = block.shape[0]
-    hh = n // 2
-    tmp = np.empty_like(block)
-    for c in range(n):                       # slow axis first (reverse order)
-        tmp[:, c] = idwt1(block[:hh, c], block[hh:, c], h)
-    out = np.empty_like(block)
-    for r in range(n):
-        out[r] = idwt1(tmp[r, :hh], tmp[r, hh:], h)
-    return out
+    hh = block.shape[0] // 2
+    lo = idwt1(block[:hh, :hh], block[hh:, :hh], h, axis=0)   # slow axis first (reverse order)
+    hi = idwt1(block[:hh, hh:], block[hh:, hh:], h, axis=0)
+    return idwt1(lo, hi, h, axis=1)
 
 
 def check_levels(N: int, levels: int) -> None:

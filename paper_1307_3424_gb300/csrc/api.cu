@@ -1,8 +1,9 @@
 // C-ABI entry points of libwproj (include/wproj.h): plan management, argument
 // checks, error reporting and timing.  All computation happens in the kernels of
-// fft.cu, build.cu, ops.cu and solve.cu.
+// fft.cu, build.cu, ops.cu, solve.cu and wavelet.cu.
 #include <math.h>
 
+#include <algorithm>
 #include <string>
 
 #include "plan.h"
@@ -129,6 +130,8 @@ void wproj_dr_defaults(wproj_dr_params *prm) {
   prm->phi_norm2 = 0.0;
   prm->power_iters = 100;
   prm->resume = 0;
+  prm->psi = 0;
+  prm->psi_levels = 4;
 }
 
 wproj_status wproj_plan_create(wproj_plan **out, const wproj_grid_desc *d) {
@@ -148,6 +151,10 @@ wproj_status wproj_plan_create(wproj_plan **out, const wproj_grid_desc *d) {
     return fail(WPROJ_ERR_INVALID_ARG, "box must be 0 or a power of two in [16, 2N]");
   if (d->value_dtype < 0 || d->value_dtype > 2) return fail(WPROJ_ERR_INVALID_ARG, "value_dtype must be 0, 1 or 2");
   if (d->index_format < 0 || d->index_format > 2) return fail(WPROJ_ERR_INVALID_ARG, "index_format must be 0, 1 or 2");
+  if (d->upsampling != 0 && d->upsampling != 1) return fail(WPROJ_ERR_INVALID_ARG, "upsampling must be 0 or 1");
+  if (d->upsampling == 1 && d->kb_support != 1)
+    return fail(WPROJ_ERR_INVALID_ARG, "upsampling = 1 (visibilities on the grid) needs kb_support = 1");
+  if (d->upsampling == 1 && d->n < 16) return fail(WPROJ_ERR_INVALID_ARG, "upsampling = 1 needs n >= 16");
   const double lmax = d->extension == WPROJ_EXT_CLAMP ? 0.5 * d->fov : d->fov;
   if (d->chirp == WPROJ_CHIRP_EXACT && 2.0 * lmax * lmax >= 1.0)
     return fail(WPROJ_ERR_INVALID_ARG, "1 - l^2 - m^2 < 0 on the sampled box (fov too large)");
@@ -157,9 +164,13 @@ wproj_status wproj_plan_create(wproj_plan **out, const wproj_grid_desc *d) {
   g.N = d->n;
   g.G = G;
   g.W = d->kb_support;
-  g.L = d->fov;
-  g.du = 1.0 / (2.0 * d->fov);
-  g.B = d->n / (2.0 * d->fov);
+  // the kernel geometry: with upsampling the chirp is sampled on the upsampled
+  // image, i.e. on a box spanning [-L/2, L/2), and the grid cell is 1/L
+  const double Lk = d->upsampling ? 0.5 * d->fov : d->fov;
+  g.L = Lk;
+  g.du = 1.0 / (2.0 * Lk);
+  g.B = d->n / (2.0 * Lk);
+  g.upsampling = d->upsampling;
   g.beta = (g.W > 1) ? M_PI * sqrt((g.W / 2.0) * (g.W / 2.0) * 1.5 * 1.5 - 0.8) : 0.0;
   g.chirp = d->chirp;
   g.extension = d->extension;
@@ -270,6 +281,9 @@ wproj_status wproj_solve_bpdn(wproj_plan *p, const void *y, double eps, const wp
   if (q.iters < 0 || q.inner_iters < 1 || !(q.gamma_frac >= 0) || !(q.lambda > 0 && q.lambda < 2) ||
       q.power_iters < 1)
     return fail(WPROJ_ERR_INVALID_ARG, "invalid DR parameters");
+  if (q.psi < 0 || q.psi > WPROJ_DAUB_MAX_P) return fail(WPROJ_ERR_INVALID_ARG, "psi: 0 or a Daubechies order");
+  if (q.psi && (q.psi_levels < 1 || p->g.N % (1 << std::min(q.psi_levels, 30)) != 0))
+    return fail(WPROJ_ERR_INVALID_ARG, "psi_levels: N must be divisible by 2^levels");
   return solve_bpdn_impl(p, static_cast<const float2 *>(y), eps, q, x_out, info, as_stream(stream));
 }
 

@@ -722,6 +722,7 @@ wproj_status wproj_batch_solve_bpdn(wproj_batch *b, const void *y, const double 
   if (q.iters < 0 || q.inner_iters < 1 || q.power_iters < 1 || !(q.lambda > 0.0 && q.lambda < 2.0) ||
       !(q.gamma_frac >= 0.0))
     return fail(WPROJ_ERR_INVALID_ARG, "batch_solve_bpdn: invalid parameters");
+  if (q.psi != 0) return fail(WPROJ_ERR_UNSUPPORTED, "batch_solve_bpdn: the batched solver uses the Dirac basis");
   for (int p = 0; p < b->np; ++p)
     if (!(eps[p] >= 0.0) || !isfinite(eps[p]))
       return fail(WPROJ_ERR_INVALID_ARG, "batch_solve_bpdn: eps must be finite and >= 0");

@@ -325,6 +325,66 @@ k_box_rows(BoxBatch bb, const float2 *__restrict__ tw) {
   }
 }
 
+// ---- separable kernel boxes (linear chirp, Eq. 5) ------------------------------------
+// exp(pi i w (l^2 + m^2)) times the separable taps is an outer product Au x Av,
+// so its 2-D inverse DFT is the outer product of two 1-D ones: K = (IDFT Au) x
+// (IDFT Av) / S^2, two length-S transforms per box instead of an S x S one.
+__global__ void k_box_outer(int nb, int S, const float2 *__restrict__ Au, const float2 *__restrict__ Av, float scale,
+                            float2 *__restrict__ K) {
+  const int64_t n = int64_t(nb) * S * S;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t b = i / (int64_t(S) * S);
+    const int P = int((i / S) % S), Q = int(i % S);
+    K[i] = cscale(cmul(Au[b * S + P], Av[b * S + Q]), scale);
+  }
+}
+
+// ---- the paper's upsampling U (Section 2.2): spectral zero-padding -----------------
+// F_G U x = P F_N x: the unitary spectrum of the image (pixel offset p - N/2 at
+// index (p - N/2) mod N) placed on the G x G grid, frequency k in [-N/2, N/2)
+// at index k mod G, zeros elsewhere.  Its adjoint crops and inverts.
+
+__global__ void k_up_in(int N, const float *__restrict__ x, const float2 *__restrict__ xc, float2 *__restrict__ out) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= int64_t(N) * N) return;
+  const int p = int(i / N), q = int(i % N), h = N / 2;
+  const float2 v = xc ? xc[i] : make_float2(x[i], 0.f);
+  out[int64_t((p - h + N) % N) * N + (q - h + N) % N] = v;
+}
+
+__global__ void k_up_scatter(int N, int G, const float2 *__restrict__ spec, float scale, float2 *__restrict__ Xt) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= int64_t(G) * G) return;
+  const int a = int(i / G), b = int(i % G), h = N / 2;
+  const int ka = a < G / 2 ? a : a - G, kb = b < G / 2 ? b : b - G;
+  float2 v = make_float2(0.f, 0.f);
+  if (ka >= -h && ka < h && kb >= -h && kb < h) v = cscale(spec[int64_t((ka + N) % N) * N + (kb + N) % N], scale);
+  Xt[i] = v;
+}
+
+__global__ void k_up_gather(int N, int G, const float2 *__restrict__ Xt2, float2 *__restrict__ spec) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= int64_t(N) * N) return;
+  const int a = int(i / N), b = int(i % N);
+  const int ka = a < N / 2 ? a : a - N, kb = b < N / 2 ? b : b - N;
+  spec[i] = Xt2[int64_t((ka + G) % G) * G + (kb + G) % G];
+}
+
+// mode 0: x_re = Re(v) (and x_c = v); mode 1: x_re = z - Re(v); v = scale * img
+__global__ void k_up_out(int N, const float2 *__restrict__ img, float scale, float *__restrict__ x_re,
+                         float2 *__restrict__ x_c, const float *__restrict__ z, int mode) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= int64_t(N) * N) return;
+  const int p = int(i / N), q = int(i % N), h = N / 2;
+  const float2 v = cscale(img[int64_t((p - h + N) % N) * N + (q - h + N) % N], scale);
+  if (mode == 0) {
+    if (x_re) x_re[i] = v.x;
+    if (x_c) x_c[i] = v;
+  } else {
+    x_re[i] = z[i] - v.x;
+  }
+}
+
 // ---- dispatch ------------------------------------------------------------------
 
 template <class K>
@@ -495,7 +555,33 @@ wproj_status bphi_adj_impl(int np, const int32_t *plist, const BProb *tab, const
   return WPROJ_OK;
 }
 
+// F U x into Xt (G x G); work: 2 N^2 complex
+wproj_status up_forward(wproj_plan *p, const float *x, const float2 *xc, float2 *work, float2 *Xt, cudaStream_t s) {
+  const int N = p->g.N, G = p->g.G;
+  float2 *a = work, *b = work + int64_t(N) * N;
+  k_up_in<<<ceil_div(int64_t(N) * N, 256), 256, 0, s>>>(N, x, xc, a);
+  WPROJ_CHECK_LAUNCH("upsampling input");
+  WPROJ_TRY(fft2d_generic(a, b, N, 1, 0, p->twiddle.as<float2>(), s));
+  k_up_scatter<<<ceil_div(int64_t(G) * G, 256), 256, 0, s>>>(N, G, b, 1.0f / N, Xt);
+  WPROJ_CHECK_LAUNCH("upsampling scatter");
+  return WPROJ_OK;
+}
+
+// (F U)^H of Xt2 into the image; work: 2 N^2 complex
+wproj_status up_adjoint(wproj_plan *p, const float2 *Xt2, float *x_re, float2 *x_c, const float *z, int mode,
+                        float2 *work, cudaStream_t s) {
+  const int N = p->g.N, G = p->g.G;
+  float2 *a = work, *b = work + int64_t(N) * N;
+  k_up_gather<<<ceil_div(int64_t(N) * N, 256), 256, 0, s>>>(N, G, Xt2, a);
+  WPROJ_CHECK_LAUNCH("upsampling gather");
+  WPROJ_TRY(fft2d_generic(a, b, N, 1, 1, p->twiddle.as<float2>(), s));
+  k_up_out<<<ceil_div(int64_t(N) * N, 256), 256, 0, s>>>(N, b, 1.0f / N, x_re, x_c, z, mode);
+  WPROJ_CHECK_LAUNCH("upsampling output");
+  return WPROJ_OK;
+}
+
 wproj_status phi_forward_fft_into(wproj_plan *p, const float *x, float2 *inter, float2 *Xt, cudaStream_t s) {
+  if (p->g.upsampling) return up_forward(p, x, nullptr, inter, Xt, s);
 #define CALL(L) phi_fwd_into_impl<L>(p, x, inter, Xt, s)
   WPROJ_LOGN_SWITCH(ilog2(p->g.G), CALL)
 #undef CALL
@@ -512,6 +598,10 @@ wproj_status init_twiddles(wproj_plan *p, cudaStream_t s) { return make_twiddles
 
 wproj_status phi_forward_fft(wproj_plan *p, const float *x, const float2 *xc, float2 *Xt, cudaStream_t s) {
   ScopedTimer t(p, TC_FFT, s);
+  if (p->g.upsampling) {
+    p->launches += 4;
+    return up_forward(p, x, xc, p->inter.as<float2>(), Xt, s);
+  }
   p->launches += 2;
 #define CALL(L) phi_fwd_impl<L>(p, x, xc, Xt, s)
   WPROJ_LOGN_SWITCH(ilog2(p->g.G), CALL)
@@ -521,6 +611,10 @@ wproj_status phi_forward_fft(wproj_plan *p, const float *x, const float2 *xc, fl
 wproj_status phi_adjoint_fft(wproj_plan *p, const float2 *Xt2, float *x_re, float2 *x_cplx,
                              const float *z, int mode, cudaStream_t s) {
   ScopedTimer t(p, TC_FFT, s);
+  if (p->g.upsampling) {
+    p->launches += 4;
+    return up_adjoint(p, Xt2, x_re, x_cplx, z, mode, p->inter.as<float2>(), s);
+  }
   p->launches += 2;
 #define CALL(L) phi_adj_impl<L>(p, Xt2, x_re, x_cplx, z, mode, s)
   WPROJ_LOGN_SWITCH(ilog2(p->g.G), CALL)
@@ -534,7 +628,29 @@ wproj_status fft2d_generic(const float2 *in, float2 *out, int n, int batch, int 
 #undef CALL
 }
 
+template <int LOGN>
+wproj_status box_fft_separable_impl(wproj_plan *p, const BoxBatch &bb, cudaStream_t s) {
+  constexpr int S = 1 << LOGN;
+  using RC = RowCfg<LOGN>;
+  const float2 *tw = p->twiddle.as<float2>();
+  WPROJ_TRY(set_smem(k_fft_rows<LOGN, +1>, RC::SMEM));
+  // the per-box tables are rebuilt for every batch, so they are transformed in place
+  float2 *Au = const_cast<float2 *>(bb.Au), *Av = const_cast<float2 *>(bb.Av);
+  k_fft_rows<LOGN, +1><<<ceil_div(bb.nb, RC::C), RC::T, RC::SMEM, s>>>(Au, Au, bb.nb, tw);
+  k_fft_rows<LOGN, +1><<<ceil_div(bb.nb, RC::C), RC::T, RC::SMEM, s>>>(Av, Av, bb.nb, tw);
+  const int64_t n = int64_t(bb.nb) * S * S;
+  k_box_outer<<<(int)std::min<int64_t>(152 * 32, ceil_div(n, 256)), 256, 0, s>>>(bb.nb, S, Au, Av,
+                                                                                1.0f / (float(S) * float(S)), bb.K);
+  WPROJ_CHECK_LAUNCH("separable boxes");
+  return WPROJ_OK;
+}
+
 wproj_status box_fft(wproj_plan *p, const BoxBatch &bb, cudaStream_t s) {
+  if (p->g.chirp == WPROJ_CHIRP_LINEAR) {   // every box is separable (mode 0)
+#define CALL(L) box_fft_separable_impl<L>(p, bb, s)
+    WPROJ_LOGN_SWITCH(ilog2(bb.S), CALL)
+#undef CALL
+  }
 #define CALL(L) box_fft_impl<L>(p, bb, s)
   WPROJ_LOGN_SWITCH(ilog2(bb.S), CALL)
 #undef CALL

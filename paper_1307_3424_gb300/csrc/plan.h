@@ -89,6 +89,7 @@ struct GridGeom {
   int chirp, extension, box;
   int value_dtype;
   int index_format;   // requested wproj_index_format
+  int upsampling;     // 1: the paper's Fourier-space upsampling U instead of Z A
   int nT;        // tiles per axis = G / tile
   int tile;      // tile side (min(32, G))
 };
@@ -155,6 +156,7 @@ struct wproj_plan {
   wproj::DevBuf ytmp;        // float2[m]
   // solver buffers
   wproj::DevBuf s_z, s_x, s_u, s_r, s_scal;   // scal: double scratch for reductions
+  wproj::DevBuf s_zi, s_alpha, s_wwork;       // wavelet Psi: Psi z, Psi^T x, transform scratch
 
   // Douglas-Rachford state kept for resume / checkpoint
   bool dr_valid = false;
@@ -198,6 +200,13 @@ wproj_status batch_phi_fwd(int logG, int np, const int32_t *plist, const BProb *
 wproj_status batch_phi_adj(int logG, int np, const int32_t *plist, const BProb *tab, const float2 *Xt2,
                            const float *inv_a, float2 *inter, float *x_re, const float *z, int mode,
                            const float2 *tw, cudaStream_t s);
+
+// wavelet.cu: the Daubechies basis; work holds N*N/2 floats
+wproj_status daubechies_taps_impl(int p, double *h_out);
+wproj_status dwt2_impl(int N, int levels, int p, const float *x, float *alpha, float *work, int64_t *launches,
+                       cudaStream_t s);
+wproj_status idwt2_impl(int N, int levels, int p, const float *alpha, float *x, float *work, int64_t *launches,
+                        cudaStream_t s);
 
 // ops.cu
 wproj_status degrid(wproj_plan *p, const float2 *Xt, float2 *y, cudaStream_t s);

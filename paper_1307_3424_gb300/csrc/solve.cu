@@ -187,15 +187,33 @@ wproj_status solve_bpdn_impl(wproj_plan *p, const float2 *y, double eps, const w
   const double mu = 1.0 / phi_norm2;
   const int64_t n = int64_t(p->g.N) * p->g.N;
   const int64_t m = p->m;
+  // Psi (Eq. 7): 0 = Dirac; else Daubechies-psi wavelets, orthonormal, so the
+  // projection onto the constraint set in coefficient space is Psi^T P(Psi z) with
+  // P the image-space projection: z, the soft threshold and the DR update live
+  // in coefficient space; the inner loop runs on the image zi = Psi z.
+  const int psi = prm.psi, lev = prm.psi_levels, N = p->g.N;
+  if (psi) {
+    WPROJ_TRY(p->s_zi.ensure(sizeof(float) * n));
+    WPROJ_TRY(p->s_alpha.ensure(sizeof(float) * n));
+    WPROJ_TRY(p->s_wwork.ensure(sizeof(float) * (n / 2 + 1)));
+  }
   float *z = p->s_z.as<float>(), *x = p->s_x.as<float>();
+  float *zi = psi ? p->s_zi.as<float>() : z;         // the image the projection starts from
+  float *alpha = psi ? p->s_alpha.as<float>() : x;   // P(z) in the basis of z
+  float *wk = p->s_wwork.as<float>();
   float2 *u = p->s_u.as<float2>(), *r = p->s_r.as<float2>();
   double *scal = p->s_scal.as<double>();
   double *part = scal + 8;
   const int nbm = grid_for(m), nbn = grid_for(n);
 
   if (!resume) {
-    // z0 = Re Phi^H y, gamma
-    WPROJ_TRY(apply_phi_adj(p, y, z, nullptr, nullptr, 0, s));
+    // z0 = Psi^T Re Phi^H y, gamma
+    if (psi) {
+      WPROJ_TRY(apply_phi_adj(p, y, x, nullptr, nullptr, 0, s));
+      WPROJ_TRY(dwt2_impl(N, lev, psi, x, z, wk, &p->launches, s));
+    } else {
+      WPROJ_TRY(apply_phi_adj(p, y, z, nullptr, nullptr, 0, s));
+    }
     ScopedTimer t(p, TC_SOLVER, s);
     k_absmax_part<<<nbn, kRedThreads, 0, s>>>(n, z, part);
     k_gamma<<<1, 1, 0, s>>>(part, nbn, prm.gamma_frac, scal);
@@ -206,8 +224,9 @@ wproj_status solve_bpdn_impl(wproj_plan *p, const float2 *y, double eps, const w
   p->dr_valid = true;
   p->dr_phi_norm2 = phi_norm2;
   for (int t_ = 0; t_ < prm.iters; ++t_) {
+    if (psi) WPROJ_TRY(idwt2_impl(N, lev, psi, z, zi, wk, &p->launches, s));
     for (int j = 0; j < prm.inner_iters; ++j) {
-      WPROJ_TRY(apply_phi_adj(p, u, x, nullptr, z, 1, s));    // x = z - Re Phi^H u
+      WPROJ_TRY(apply_phi_adj(p, u, x, nullptr, zi, 1, s));   // x = zi - Re Phi^H u
       WPROJ_TRY(apply_phi(p, x, nullptr, r, s));               // r = Phi x
       ScopedTimer t(p, TC_SOLVER, s);
       k_dual_residual<<<nbm, kRedThreads, 0, s>>>(m, u, r, y, float(1.0 / mu), part);
@@ -216,20 +235,25 @@ wproj_status solve_bpdn_impl(wproj_plan *p, const float2 *y, double eps, const w
       WPROJ_CHECK_LAUNCH("dual step");
       p->launches += 3;
     }
-    WPROJ_TRY(apply_phi_adj(p, u, x, nullptr, z, 1, s));      // x = P_B(z)
+    WPROJ_TRY(apply_phi_adj(p, u, x, nullptr, zi, 1, s));     // x = P_B(zi)
+    if (psi) WPROJ_TRY(dwt2_impl(N, lev, psi, x, alpha, wk, &p->launches, s));
     ScopedTimer t(p, TC_SOLVER, s);
-    k_dr_update<<<nbn, kRedThreads, 0, s>>>(n, x, z, float(prm.lambda), scal);
+    k_dr_update<<<nbn, kRedThreads, 0, s>>>(n, alpha, z, float(prm.lambda), scal);
     WPROJ_CHECK_LAUNCH("dr update");
     p->launches += 1;
   }
-  if (prm.iters == 0) WPROJ_CUDA(cudaMemcpyAsync(x, z, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
+  if (prm.iters == 0) {
+    if (psi) WPROJ_TRY(idwt2_impl(N, lev, psi, z, x, wk, &p->launches, s));
+    else WPROJ_CUDA(cudaMemcpyAsync(x, z, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
+  }
   WPROJ_CUDA(cudaMemcpyAsync(x_out, x, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
   if (info) {
     // residual ||y - Phi x|| and ||x||_1
     WPROJ_TRY(apply_phi(p, x, nullptr, r, s));
     k_resid_part<<<nbm, kRedThreads, 0, s>>>(m, r, y, part);
     k_sum_parts<<<1, 1, 0, s>>>(part, nbm, scal + 4);
-    k_sum_part<1><<<nbn, kRedThreads, 0, s>>>(n, x, part);
+    if (psi) WPROJ_TRY(dwt2_impl(N, lev, psi, x, alpha, wk, &p->launches, s));
+    k_sum_part<1><<<nbn, kRedThreads, 0, s>>>(n, alpha, part);
     k_sum_parts<<<1, 1, 0, s>>>(part, nbn, scal + 5);
     WPROJ_CHECK_LAUNCH("solve info");
     double h[4];   // gamma, ||d||, ||y - Phi x||^2, ||x||_1

@@ -1,0 +1,329 @@
+// The Daubechies wavelet sparsity basis Psi of the BPDN problem (Eq. 7; the
+// paper's second dictionary is Daubechies 8, Section 4): the periodic,
+// orthonormal, separable 2-D transform in the Mallat layout.
+//
+// One dyadic level is one kernel: a CTA stages the input region of its output
+// tile in shared memory (periodic wrap), filters the fast axis into two shared
+// intermediates and the slow axis into the four sub-bands.  The image at this
+// size lives in L2, so the levels are latency- rather than bandwidth-bound; the
+// point of the fused level is one launch and one pass over global memory per
+// level instead of one per axis.
+//
+// Conventions (one level on an even length n, h = n/2, i in [0, h)):
+//   a_i = sum_k h_k x_{(2i + k) mod n},  d_i = sum_k g_k x_{(2i + k) mod n},
+//   g_k = (-1)^k h_{2p-1-k}.
+// The synthesis is the transpose: x_j = sum over k = j mod 2 of
+//   h_k a_{((j - k)/2) mod h} + g_k d_{((j - k)/2) mod h}.
+#include <complex>
+#include <cmath>
+#include <vector>
+
+#include "plan.h"
+
+namespace wproj {
+
+constexpr int kMaxTaps = 2 * WPROJ_DAUB_MAX_P;
+constexpr int kWT = 16;                       // analysis output tile (per sub-band); synthesis input tile
+constexpr int kWIn = 2 * kWT + kMaxTaps - 2;  // staged input side of an analysis tile
+constexpr int kWSyn = kWT + kMaxTaps / 2 - 1; // staged sub-band side of a synthesis tile
+constexpr int kWThreads = 256;
+
+struct Taps {
+  float h[kMaxTaps];
+  float g[kMaxTaps];
+  int len;
+};
+
+// ---- the taps: Daubechies' spectral factorisation, in double on the host ------
+
+namespace {
+
+using cd = std::complex<double>;
+
+cd poly_eval(const std::vector<double> &c, cd z) {   // c[0] + c[1] z + ...
+  cd v = 0;
+  for (size_t i = c.size(); i-- > 0;) v = v * z + c[i];
+  return v;
+}
+
+// all roots of c[0] + c[1] z + ... + c[d] z^d by the Weierstrass (Durand-Kerner)
+// simultaneous iteration, then Newton steps on each root
+std::vector<cd> poly_roots(const std::vector<double> &c) {
+  const int d = int(c.size()) - 1;
+  std::vector<cd> r(d);
+  if (d <= 0) return r;
+  const double lead = c[d];
+  // start on a circle of the Cauchy bound, at angles that avoid symmetry
+  double bound = 0;
+  for (int i = 0; i < d; ++i) bound = std::max(bound, std::abs(c[i] / lead));
+  bound = 1.0 + bound;
+  for (int i = 0; i < d; ++i) r[i] = std::polar(0.5 * bound, 2.0 * M_PI * i / d + 0.4);
+  for (int it = 0; it < 2000; ++it) {
+    double change = 0;
+    for (int i = 0; i < d; ++i) {
+      cd den = lead;
+      for (int j = 0; j < d; ++j)
+        if (j != i) den *= (r[i] - r[j]);
+      const cd step = poly_eval(c, r[i]) / den;
+      r[i] -= step;
+      change = std::max(change, std::abs(step) / std::max(1.0, std::abs(r[i])));
+    }
+    if (change < 1e-16) break;
+  }
+  std::vector<double> dc(d);
+  for (int i = 1; i <= d; ++i) dc[i - 1] = i * c[i];
+  for (int i = 0; i < d; ++i)
+    for (int it = 0; it < 3; ++it) {
+      const cd f = poly_eval(c, r[i]), fp = poly_eval(dc, r[i]);
+      if (std::abs(fp) == 0) break;
+      r[i] -= f / fp;
+    }
+  return r;
+}
+
+}  // namespace
+
+// Low-pass taps of the extremal-phase Daubechies wavelet with p vanishing
+// moments: |H|^2 = cos^{2p}(w/2) P_p(sin^2(w/2)), P_p(y) = sum_{k<p} C(p-1+k, k) y^k;
+// every root y_k of P_p contributes the root of z^2 - (2 - 4 y_k) z + 1 inside the
+// unit circle; H(z) = (1 + z)^p prod (z - z_k), scaled to sum sqrt(2), in the
+// order whose partial energies are front-loaded.
+wproj_status daubechies_taps_impl(int p, double *h_out) {
+  if (p < 1 || p > WPROJ_DAUB_MAX_P) return fail(WPROJ_ERR_INVALID_ARG, "Daubechies order out of range");
+  std::vector<double> P(p);
+  double binom = 1.0;                           // C(p-1+k, k)
+  for (int k = 0; k < p; ++k) {
+    P[k] = binom;
+    binom = binom * double(p + k) / double(k + 1);
+  }
+  const std::vector<cd> yk = poly_roots(P);
+  std::vector<cd> poly(1, cd(1.0));             // coefficient of z^i at index i
+  auto mul_linear = [&](cd root) {              // poly *= (z - root)
+    std::vector<cd> out(poly.size() + 1, cd(0));
+    for (size_t i = 0; i < poly.size(); ++i) {
+      out[i + 1] += poly[i];
+      out[i] -= root * poly[i];
+    }
+    poly.swap(out);
+  };
+  for (int i = 0; i < p; ++i) mul_linear(cd(-1.0));
+  for (const cd &y : yk) {
+    const cd b = 2.0 - 4.0 * y;
+    const cd disc = std::sqrt(b * b - 4.0);
+    const cd z1 = 0.5 * (b + disc), z2 = 0.5 * (b - disc);
+    mul_linear(std::abs(z1) < 1.0 ? z1 : z2);
+  }
+  const int L = 2 * p;
+  std::vector<double> h(L);
+  double sum = 0;
+  for (int i = 0; i < L; ++i) {
+    h[i] = poly[i].real();
+    sum += h[i];
+  }
+  for (int i = 0; i < L; ++i) h[i] *= std::sqrt(2.0) / sum;
+  double ef = 0, er = 0, cf = 0, cr = 0;
+  for (int i = 0; i < L; ++i) {
+    cf += h[i] * h[i];
+    cr += h[L - 1 - i] * h[L - 1 - i];
+    ef += cf;
+    er += cr;
+  }
+  for (int i = 0; i < L; ++i) h_out[i] = er > ef ? h[L - 1 - i] : h[i];
+  return WPROJ_OK;
+}
+
+namespace {
+
+Taps make_taps(const double *h, int L) {
+  Taps t{};
+  t.len = L;
+  for (int k = 0; k < L; ++k) {
+    t.h[k] = float(h[k]);
+    t.g[k] = float(((k & 1) ? -1.0 : 1.0) * h[L - 1 - k]);
+  }
+  return t;
+}
+
+__device__ __forceinline__ int wrap(int i, int n) {
+  i %= n;
+  return i < 0 ? i + n : i;
+}
+
+// One analysis level: src (n x n, row stride lds) -> the four sub-bands; the
+// low-low band to ll (row stride ldl), the three others into the Mallat blocks of
+// coef (row stride ldc).
+__global__ void __launch_bounds__(kWThreads)
+k_dwt_level(const float *__restrict__ src, int lds, int n, const Taps t, float *__restrict__ ll, int ldl,
+            float *__restrict__ coef, int ldc) {
+  __shared__ float in[kWIn][kWIn + 1];
+  __shared__ float lo[kWIn][kWT + 1], hi[kWIn][kWT + 1];
+  const int h = n / 2, L = t.len;
+  const int i0 = blockIdx.y * kWT, c0 = blockIdx.x * kWT;
+  const int span = 2 * kWT + L - 2;
+  for (int e = threadIdx.x; e < span * span; e += kWThreads) {
+    const int r = e / span, c = e % span;
+    in[r][c] = src[int64_t(wrap(2 * i0 + r, n)) * lds + wrap(2 * c0 + c, n)];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < span * kWT; e += kWThreads) {      // fast axis
+    const int r = e / kWT, c = e % kWT;
+    float a = 0.f, d = 0.f;
+    for (int k = 0; k < L; ++k) {
+      const float v = in[r][2 * c + k];
+      a = fmaf(t.h[k], v, a);
+      d = fmaf(t.g[k], v, d);
+    }
+    lo[r][c] = a;
+    hi[r][c] = d;
+  }
+  __syncthreads();
+  const int i = threadIdx.x / kWT, c = threadIdx.x % kWT;        // slow axis
+  float s_ll = 0.f, s_lh = 0.f, s_hl = 0.f, s_hh = 0.f;
+  for (int k = 0; k < L; ++k) {
+    const float vl = lo[2 * i + k][c], vh = hi[2 * i + k][c];
+    s_ll = fmaf(t.h[k], vl, s_ll);
+    s_lh = fmaf(t.h[k], vh, s_lh);
+    s_hl = fmaf(t.g[k], vl, s_hl);
+    s_hh = fmaf(t.g[k], vh, s_hh);
+  }
+  const int gi = i0 + i, gc = c0 + c;
+  if (gi < h && gc < h) {
+    ll[int64_t(gi) * ldl + gc] = s_ll;
+    coef[int64_t(gi) * ldc + h + gc] = s_lh;         // low slow, high fast
+    coef[int64_t(h + gi) * ldc + gc] = s_hl;         // high slow, low fast
+    coef[int64_t(h + gi) * ldc + h + gc] = s_hh;
+  }
+}
+
+// One synthesis level: the low-low band ll (row stride ldl) and the three other
+// bands of coef (row stride ldc) -> dst (n x n, row stride ldd).
+__global__ void __launch_bounds__(kWThreads)
+k_idwt_level(const float *__restrict__ ll, int ldl, const float *__restrict__ coef, int ldc, int n, const Taps t,
+             float *__restrict__ dst, int ldd) {
+  __shared__ float sb[4][kWSyn][kWSyn + 1];
+  __shared__ float lo[kWSyn][2 * kWT + 1], hi[kWSyn][2 * kWT + 1];
+  const int h = n / 2, L = t.len;
+  const int j10 = blockIdx.y * 2 * kWT, j20 = blockIdx.x * 2 * kWT;
+  const int off = L / 2 - 1;                      // staged index = band index - (j0/2 - off)
+  const int span = kWT + off;
+  const int b1 = j10 / 2 - off, b2 = j20 / 2 - off;
+  for (int e = threadIdx.x; e < span * span; e += kWThreads) {
+    const int r = e / span, c = e % span;
+    const int gi = wrap(b1 + r, h), gc = wrap(b2 + c, h);
+    sb[0][r][c] = ll[int64_t(gi) * ldl + gc];
+    sb[1][r][c] = coef[int64_t(gi) * ldc + h + gc];
+    sb[2][r][c] = coef[int64_t(h + gi) * ldc + gc];
+    sb[3][r][c] = coef[int64_t(h + gi) * ldc + h + gc];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < span * 2 * kWT; e += kWThreads) {   // fast axis
+    const int r = e / (2 * kWT), jj = e % (2 * kWT);
+    float a = 0.f, d = 0.f;
+    for (int k = jj & 1; k < L; k += 2) {
+      const int q = (jj - k) / 2 + off;
+      a = fmaf(t.h[k], sb[0][r][q], fmaf(t.g[k], sb[1][r][q], a));
+      d = fmaf(t.h[k], sb[2][r][q], fmaf(t.g[k], sb[3][r][q], d));
+    }
+    lo[r][jj] = a;
+    hi[r][jj] = d;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 4 * kWT * kWT; e += kWThreads) {    // slow axis
+    const int ii = e / (2 * kWT), jj = e % (2 * kWT);
+    float v = 0.f;
+    for (int k = ii & 1; k < L; k += 2) {
+      const int q = (ii - k) / 2 + off;
+      v = fmaf(t.h[k], lo[q][jj], fmaf(t.g[k], hi[q][jj], v));
+    }
+    const int g1 = j10 + ii, g2 = j20 + jj;
+    if (g1 < n && g2 < n) dst[int64_t(g1) * ldd + g2] = v;
+  }
+}
+
+wproj_status check_psi(int N, int levels, int p) {
+  if (p < 1 || p > WPROJ_DAUB_MAX_P) return fail(WPROJ_ERR_INVALID_ARG, "Daubechies order out of range");
+  if (N < 2 || levels < 1 || levels > 30 || N % (1 << levels) != 0)
+    return fail(WPROJ_ERR_INVALID_ARG, "n must be divisible by 2^levels");
+  return WPROJ_OK;
+}
+
+}  // namespace
+
+// alpha = Psi^T x.  work: N*N/2 floats (two ping-pong low-low bands).
+wproj_status dwt2_impl(int N, int levels, int p, const float *x, float *alpha, float *work, int64_t *launches,
+                       cudaStream_t s) {
+  WPROJ_TRY(check_psi(N, levels, p));
+  double hd[kMaxTaps];
+  WPROJ_TRY(daubechies_taps_impl(p, hd));
+  const Taps t = make_taps(hd, 2 * p);
+  float *ping[2] = {work, work + int64_t(N) * N / 4};
+  const float *src = x;
+  int lds = N, n = N;
+  for (int lv = 0; lv < levels; ++lv) {
+    const int h = n / 2;
+    const bool last = lv == levels - 1;
+    float *ll = last ? alpha : ping[lv & 1];
+    const int ldl = last ? N : h;
+    const dim3 grid(ceil_div(h, kWT), ceil_div(h, kWT));
+    k_dwt_level<<<grid, kWThreads, 0, s>>>(src, lds, n, t, ll, ldl, alpha, N);
+    WPROJ_CHECK_LAUNCH("wavelet analysis level");
+    src = ll;
+    lds = ldl;
+    n = h;
+  }
+  if (launches) *launches += levels;
+  return WPROJ_OK;
+}
+
+// x = Psi alpha.  work: N*N/2 floats.
+wproj_status idwt2_impl(int N, int levels, int p, const float *alpha, float *x, float *work, int64_t *launches,
+                        cudaStream_t s) {
+  WPROJ_TRY(check_psi(N, levels, p));
+  double hd[kMaxTaps];
+  WPROJ_TRY(daubechies_taps_impl(p, hd));
+  const Taps t = make_taps(hd, 2 * p);
+  float *ping[2] = {work, work + int64_t(N) * N / 4};
+  const float *ll = alpha;
+  int ldl = N;
+  int n = N >> (levels - 1);
+  for (int lv = levels - 1; lv >= 0; --lv) {
+    const bool last = lv == 0;
+    float *dst = last ? x : ping[lv & 1];
+    const int ldd = last ? N : n;
+    const dim3 grid(ceil_div(n, 2 * kWT), ceil_div(n, 2 * kWT));
+    k_idwt_level<<<grid, kWThreads, 0, s>>>(ll, ldl, alpha, N, n, t, dst, ldd);
+    WPROJ_CHECK_LAUNCH("wavelet synthesis level");
+    ll = dst;
+    ldl = ldd;
+    n *= 2;
+  }
+  if (launches) *launches += levels;
+  return WPROJ_OK;
+}
+
+}  // namespace wproj
+
+using namespace wproj;
+
+extern "C" {
+
+wproj_status wproj_daubechies_taps(int32_t p, double *h_out) {
+  if (!h_out) return fail(WPROJ_ERR_INVALID_ARG, "null output");
+  return daubechies_taps_impl(p, h_out);
+}
+
+wproj_status wproj_dwt2(int32_t n, int32_t levels, int32_t p, const float *x, float *alpha, float *work,
+                        void *stream) {
+  if (!x || !alpha || !work) return fail(WPROJ_ERR_INVALID_ARG, "null pointer");
+  if (x == alpha) return fail(WPROJ_ERR_INVALID_ARG, "x and alpha must not alias");
+  return dwt2_impl(n, levels, p, x, alpha, work, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+wproj_status wproj_idwt2(int32_t n, int32_t levels, int32_t p, const float *alpha, float *x, float *work,
+                         void *stream) {
+  if (!x || !alpha || !work) return fail(WPROJ_ERR_INVALID_ARG, "null pointer");
+  if (x == alpha) return fail(WPROJ_ERR_INVALID_ARG, "x and alpha must not alias");
+  return idwt2_impl(n, levels, p, alpha, x, work, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

@@ -33,6 +33,7 @@ EXPORTED = [
     "wproj_batch_get_info", "wproj_gemm_bf16", "wproj_mlp_num_params", "wproj_mlp_create",
     "wproj_mlp_destroy", "wproj_mlp_set_params", "wproj_mlp_get_params", "wproj_mlp_targets",
     "wproj_mlp_forward", "wproj_mlp_gradients", "wproj_mlp_train", "wproj_build_kernels_learned",
+    "wproj_daubechies_taps", "wproj_dwt2", "wproj_idwt2",
 ]
 
 
@@ -45,7 +46,7 @@ class WprojError(RuntimeError):
 class GridDesc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("kb_support", ctypes.c_int32), ("fov", ctypes.c_double),
                 ("chirp", ctypes.c_int32), ("extension", ctypes.c_int32), ("box", ctypes.c_int32),
-                ("value_dtype", ctypes.c_int32), ("index_format", ctypes.c_int32)]
+                ("value_dtype", ctypes.c_int32), ("index_format", ctypes.c_int32), ("upsampling", ctypes.c_int32)]
 
 
 class CSR(ctypes.Structure):
@@ -60,7 +61,7 @@ class DRParams(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("inner_iters", ctypes.c_int32),
                 ("gamma_frac", ctypes.c_double), ("lambda_", ctypes.c_double),
                 ("phi_norm2", ctypes.c_double), ("power_iters", ctypes.c_int32),
-                ("resume", ctypes.c_int32)]
+                ("resume", ctypes.c_int32), ("psi", ctypes.c_int32), ("psi_levels", ctypes.c_int32)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -143,6 +144,9 @@ def lib() -> ctypes.CDLL:
         "wproj_batch_solve_bpdn": [vp, vp, P(dbl), P(DRParams), vp, vp],
         "wproj_batch_get_info": [vp, P(BatchInfo)],
         "wproj_gemm_bf16": [i32, i32, i32, vp, vp, vp, vp, i32, vp],
+        "wproj_daubechies_taps": [i32, P(dbl)],
+        "wproj_dwt2": [i32, i32, i32, vp, vp, vp, vp],
+        "wproj_idwt2": [i32, i32, i32, vp, vp, vp, vp],
         "wproj_mlp_create": [P(vp)],
         "wproj_mlp_destroy": [vp],
         "wproj_mlp_set_params": [vp, vp, vp],
@@ -262,16 +266,18 @@ class Plan:
     """A libwproj plan: geometry, the built G and its work buffers."""
 
     def __init__(self, n: int, fov: float, kb_support: int = 4, chirp: str = "exact",
-                 extension: str = "full", box="G", value_dtype: str = "f32", index_format: str = "auto"):
+                 extension: str = "full", box="G", value_dtype: str = "f32", index_format: str = "auto",
+                 upsampling: bool = False):
         """box: "G" (default) the exact S = 2N box, "rule" the S(w) rule, or a
-        fixed power of two."""
+        fixed power of two.  upsampling=True: the paper's operator C-hat F U
+        (visibilities on the grid, kb_support=1, grid cells 1/fov)."""
         self._h = ctypes.c_void_p()
         self.n = n
         self.G = 2 * n
         self.value_dtype = value_dtype
         box_i = 2 * n if box in ("G", None) else (0 if box == "rule" else int(box))
         d = GridDesc(n, kb_support, float(fov), CHIRP[chirp], EXTENSION[extension], box_i,
-                     VALUE_DTYPE[value_dtype], INDEX_FORMAT[index_format])
+                     VALUE_DTYPE[value_dtype], INDEX_FORMAT[index_format], 1 if upsampling else 0)
         self.desc = d
         self.m = 0
         _check(lib().wproj_plan_create(ctypes.byref(self._h), ctypes.byref(d)))
@@ -357,12 +363,15 @@ class Plan:
     def solve_bpdn(self, y: torch.Tensor, eps: float, iters: int = 50, inner_iters: int = 10,
                    gamma_frac: float = 1e-2, lam: float = 1.0, phi_norm2: float = 0.0,
                    power_iters: int = 100, x_out: torch.Tensor | None = None, sync: bool = True,
-                   resume: bool = False, stream=None):
-        """Douglas-Rachford BPDN.  resume=True continues from the plan's state
-        (the previous solve or dr_state_set) instead of z = Re Phi^H y, u = 0."""
+                   resume: bool = False, psi: int = 0, psi_levels: int = 4, stream=None):
+        """Douglas-Rachford BPDN (Eq. 7).  psi = 0: Dirac basis; psi = p: Daubechies
+        wavelets with p vanishing moments (8 = Db8) over psi_levels levels; the
+        returned image is x = Psi alpha.  resume=True continues from the plan's
+        state (the previous solve or dr_state_set) instead of z = Psi^T Re Phi^H y, u = 0."""
         if y.dtype != torch.complex64 or y.numel() != self.m:
             raise WprojError(ERR_INVALID_ARG, f"y must be a complex64 tensor of {self.m} visibilities")
-        prm = DRParams(iters, inner_iters, gamma_frac, lam, phi_norm2, power_iters, 1 if resume else 0)
+        prm = DRParams(iters, inner_iters, gamma_frac, lam, phi_norm2, power_iters, 1 if resume else 0,
+                       psi, psi_levels)
         if x_out is None:
             x_out = torch.empty((self.n, self.n), dtype=torch.float32, device=y.device)
         info = SolveInfo() if sync else None
@@ -418,6 +427,35 @@ def fft2d(x: torch.Tensor, inverse: bool = False, out: torch.Tensor | None = Non
         out = torch.empty_like(x)
     _check(lib().wproj_fft2d(_ptr(x), _ptr(out), n, batch, 1 if inverse else 0, _stream(stream)))
     return out
+
+
+def daubechies_taps(p: int) -> list[float]:
+    """Low-pass analysis taps (2p) of the extremal-phase Daubechies wavelet with p
+    vanishing moments."""
+    out = (ctypes.c_double * (2 * p))() if p > 0 else (ctypes.c_double * 1)()
+    _check(lib().wproj_daubechies_taps(p, out))
+    return list(out)
+
+
+def _wavelet(fn, src: torch.Tensor, levels: int, p: int, out, stream):
+    if src.dtype != torch.float32 or src.dim() != 2 or src.shape[0] != src.shape[1] or not src.is_contiguous():
+        raise WprojError(ERR_INVALID_ARG, "expected a contiguous (n, n) float32 tensor")
+    n = src.shape[0]
+    if out is None:
+        out = torch.empty_like(src)
+    work = torch.empty(max(1, n * n // 2), dtype=torch.float32, device=src.device)
+    _check(fn(n, levels, p, _ptr(src), _ptr(out), _ptr(work), _stream(stream)))
+    return out
+
+
+def dwt2(x: torch.Tensor, levels: int = 4, p: int = 8, out: torch.Tensor | None = None, stream=None):
+    """alpha = Psi^T x: periodic 2-D Daubechies-p analysis in the Mallat layout."""
+    return _wavelet(lib().wproj_dwt2, x, levels, p, out, stream)
+
+
+def idwt2(alpha: torch.Tensor, levels: int = 4, p: int = 8, out: torch.Tensor | None = None, stream=None):
+    """x = Psi alpha: the synthesis (inverse and transpose of dwt2)."""
+    return _wavelet(lib().wproj_idwt2, alpha, levels, p, out, stream)
 
 
 class Batch:
