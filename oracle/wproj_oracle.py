@@ -33,6 +33,9 @@ Readings of the paper taken here (the paper is silent or inconsistent):
   * The chirp is sampled on an S x S box spanning [-L, L)^2 (S = G is exact);
     outside the field of view it is either evaluated as is ('full') or with
     the coordinates clamped to the field of view ('clamp').
+  * Direction-dependent effects (Section 3.2 claims the per-row threshold
+    applies to all of them): a screen A(l, m) per visibility multiplies the
+    chirp in image space before the FFT, sampled at the same G x G points.
   * KB: W = 4, oversampling 2, beta from Beatty, Nishimura & Pauly (2005);
     taps at j0-W/2+1 .. j0+W/2 (half-open at a cell boundary).
 
@@ -181,7 +184,7 @@ class Geometry:
         self.a = correction(N, W, self.beta)
 
 
-def kernel_box(geo: Geometry, u: float, v: float, w: float, S: int):
+def kernel_box(geo: Geometry, u: float, v: float, w: float, S: int, screen=None):
     """Unthresholded kernel of one visibility on its S x S box.
 
     Returns (K, j0u, j0v) with K[su mod S, sv mod S] the weight of grid cell
@@ -193,6 +196,12 @@ def kernel_box(geo: Geometry, u: float, v: float, w: float, S: int):
     C-hat of Eq. 8, Section 3.2: chirp in real space, then a 2-D FFT),
     T[t] = kb(du - tu) kb(dv - tv) the gridding taps at the sub-grid offset.
     At S = G this is the exact circular convolution of C-hat with the taps.
+
+    screen: an optional direction-dependent effect (Section 3.2: the threshold
+    makes no assumption on a row's structure, so it applies to any such
+    effect): a G x G complex array sampled at the chirp's points, index P
+    holding offset P - G/2 (pixel p of the image sits at index p + N/2).  The
+    row is then the FFT of (chirp x screen), convolved with the taps.  Needs S = G.
     """
     gu, gv = u / geo.du, v / geo.du
     j0u, j0v = math.floor(gu), math.floor(gv)
@@ -200,6 +209,11 @@ def kernel_box(geo: Geometry, u: float, v: float, w: float, S: int):
     tv = tap_weights(gv - j0v, geo.W, geo.beta)
     lp = box_coords(S, geo.L, geo.extension)
     c = chirp(lp[:, None], lp[None, :], w, geo.chirp_kind)
+    if screen is not None:
+        screen = np.asarray(screen)
+        if S != geo.G or screen.shape != (S, S):
+            raise ValueError("a screen needs the full box S = G and a G x G array")
+        c = c * screen
     Chat = centred_dft2(c)
     # R[s] = Chat[-s]; then Chat[t - s] = R[s - t] = roll(R, t)[s]
     R = np.roll(Chat[::-1, ::-1], 1, axis=(0, 1))
@@ -292,9 +306,9 @@ def select_bisect(values, e: float, iters: int = 200):
 # ----------------------------------------------------------------------------
 
 
-def kernel_row(geo: Geometry, u: float, v: float, w: float, S: int, e: float):
+def kernel_row(geo: Geometry, u: float, v: float, w: float, S: int, e: float, screen=None):
     """Sparse row k of G: (columns ascending, values) after thresholding."""
-    K, j0u, j0v = kernel_box(geo, u, v, w, S)
+    K, j0u, j0v = kernel_box(geo, u, v, w, S, screen)
     cols = box_columns(geo, j0u, j0v, S)
     kept = select_sort(K, cols, e)
     c = cols.ravel()[kept]
@@ -313,14 +327,17 @@ def row_box(geo: Geometry, w: float, S) -> int:
     return int(S)
 
 
-def build_G(geo: Geometry, uvw: np.ndarray, e: float, S=None):
-    """CSR G (M x G^2, complex128), one thresholded kernel per visibility."""
+def build_G(geo: Geometry, uvw: np.ndarray, e: float, S=None, screens=None, screen_id=None):
+    """CSR G (M x G^2, complex128), one thresholded kernel per visibility.
+    screens (n x G x G) with screen_id (M ints) attach a direction-dependent
+    screen to every row (kernel_box); then S must be None (the full box)."""
     M = uvw.shape[0]
     rows, cols, vals = [], [], []
     ptr = [0]
     for k in range(M):
         Sk = row_box(geo, uvw[k, 2], S)
-        c, v = kernel_row(geo, uvw[k, 0], uvw[k, 1], uvw[k, 2], Sk, e)
+        scr = None if screens is None else screens[int(screen_id[k])]
+        c, v = kernel_row(geo, uvw[k, 0], uvw[k, 1], uvw[k, 2], Sk, e, scr)
         cols.append(c)
         vals.append(v)
         ptr.append(ptr[-1] + c.size)
@@ -475,6 +492,23 @@ def visibilities_direct(geo: Geometry, x, uvw):
         c = chirp(l[:, None], l[None, :], w, geo.chirp_kind)
         ph = np.exp(-2j * np.pi * (u * l[:, None] + v * l[None, :]))
         y[k] = np.sum(np.asarray(x) * c * ph) / geo.G
+    return y
+
+
+def visibilities_direct_dde(geo: Geometry, x, uvw, screens, screen_id):
+    """visibilities_direct with a direction-dependent screen per visibility:
+      y_k = (1/G) sum_{p,q} x_pq A_k(l_p, m_q) C(l_p, m_q; w_k) exp(-2 pi i (u_k l_p + v_k m_q)),
+    A_k = screens[screen_id[k]] read at the image's pixels (index p + N/2)."""
+    N = geo.N
+    l = (np.arange(N) - N // 2) * geo.dl
+    pix = np.arange(N) + N // 2
+    y = np.empty(uvw.shape[0], dtype=np.complex128)
+    for k in range(uvw.shape[0]):
+        u, v, w = uvw[k]
+        A = np.asarray(screens[int(screen_id[k])])[np.ix_(pix, pix)]
+        c = chirp(l[:, None], l[None, :], w, geo.chirp_kind)
+        ph = np.exp(-2j * np.pi * (u * l[:, None] + v * l[None, :]))
+        y[k] = np.sum(np.asarray(x) * A * c * ph) / geo.G
     return y
 
 

@@ -287,3 +287,28 @@ def paper_problem(N: int, coverage: float, seed: int = 0, wd: float | None = Non
     uvw = np.ascontiguousarray(np.concatenate([(cells + 1e-9) / L, w[:, None]], axis=1))
     wl = Workload(f"paper{N}_cov{coverage}", N=N, n_blobs=n_blobs, M=M, uv="grid", wd_max=1.0, e=0.75)
     return Problem(wl, L, x, uvw, wdv, rng)
+
+
+def dde_screens(n_screens: int, N: int, L: float, seed: int = 0, beam_fwhm: float = 1.2,
+                pointing: float = 0.05, phase_rad: float = 0.5, modes: int = 3) -> np.ndarray:
+    """Synthetic direction-dependent screens (A-projection style), n x G x G
+    complex64 on the chirp's sample points of the padded field of view: index P
+    holds offset P - G/2, i.e. l = (P - G/2) L / N (pixel p of the image at
+    index p + N/2).  Each screen is a Gaussian primary beam of full width at
+    half maximum beam_fwhm * L, pointed off centre by up to pointing * L, times
+    a smooth phase screen of `modes` plane waves of at most two cycles across
+    the field of view and amplitude phase_rad radians each."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    G = 2 * N
+    l = (np.arange(G) - G // 2) * (L / N)
+    sig = beam_fwhm * L / (2.0 * math.sqrt(2.0 * math.log(2.0)))
+    out = np.empty((n_screens, G, G), dtype=np.complex64)
+    for j in range(n_screens):
+        l0, m0 = rng.uniform(-pointing, pointing, 2) * L
+        beam = np.exp(-((l[:, None] - l0) ** 2 + (l[None, :] - m0) ** 2) / (2.0 * sig * sig))
+        phase = np.zeros((G, G))
+        for _ in range(modes):
+            ku, kv = rng.uniform(-2.0, 2.0, 2) / L
+            phase += phase_rad * np.cos(2.0 * math.pi * (ku * l[:, None] + kv * l[None, :]) + rng.uniform(0, 2 * math.pi))
+        out[j] = (beam * np.exp(1j * phase)).astype(np.complex64)
+    return out
