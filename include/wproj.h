@@ -194,6 +194,24 @@ wproj_status wproj_plan_destroy(wproj_plan *p);
 wproj_status wproj_build_kernels(wproj_plan *p, const double *uvw, int64_t m, double e,
                                  void *stream, wproj_csr *out);
 
+/* Direction-dependent effects (Section 3.2: the per-row threshold assumes nothing
+ * about a row's structure, so it applies to any image-space modulation, not only
+ * the w-chirp).  A screen A(l, m) multiplies the chirp of every row it is
+ * attached to before the FFT: row k is FFT(chirp_k x A_{screen_id[k]}), convolved
+ * with the gridding taps and thresholded like any other row.
+ * wproj_set_screens: n_screens screens, complex64 [n_screens][G][G] row-major
+ * (host or device; copied into the plan), sample (a, b) at
+ * l = (a - G/2) L / N, m = (b - G/2) L / N over the padded field of view (image
+ * pixel (p, q) at (p + N/2, q + N/2)).  n_screens = 0 drops them.  Non-finite
+ * samples -> WPROJ_ERR_INVALID_ARG.  Invalidates the current G.  Synchronous.
+ * wproj_build_kernels_dde: as wproj_build_kernels with screen_id (device int32[m],
+ * each in [0, n_screens), else WPROJ_ERR_INVALID_ARG) naming every row's screen.
+ * Needs a plan with the full kernel box (box = G; else WPROJ_ERR_UNSUPPORTED),
+ * as a screen is sampled at the full box's points. */
+wproj_status wproj_set_screens(wproj_plan *p, const void *screens, int32_t n_screens, void *stream);
+wproj_status wproj_build_kernels_dde(wproj_plan *p, const double *uvw, int64_t m, const int32_t *screen_id,
+                                     double e, void *stream);
+
 /* View of the current G (WPROJ_ERR_NOT_BUILT before the first build). */
 wproj_status wproj_get_csr(const wproj_plan *p, wproj_csr *out);
 
@@ -245,7 +263,7 @@ wproj_status wproj_solve_bpdn(wproj_plan *p, const void *y, double eps,
                               wproj_solve_info *info, void *stream);
 
 /* ||Phi||^2 of the real-image operator by `iters` power iterations from the
- * constant image 1/N (synchronous). */
+ * unit impulse at the image centre (synchronous). */
 wproj_status wproj_power_norm2(wproj_plan *p, int32_t iters, double *out, void *stream);
 
 /* Checkpoint / resume of the Douglas-Rachford state: z (N x N float32; wavelet

@@ -542,8 +542,11 @@ def soft(a, gamma):
 
 def power_norm2(apply, apply_adj, N: int, iters: int = 100):
     """||Phi||^2 of the real-image operator by power iteration on Re Phi^H Phi,
-    starting from the constant image 1/N."""
-    x = np.full((N, N), 1.0 / N)
+    starting from the unit impulse at the image centre (its spectrum is flat, so
+    no row of Phi is orthogonal to it; the constant image has only the zero
+    frequency and is annihilated by on-grid sampling at w = 0 that misses it)."""
+    x = np.zeros((N, N))
+    x[N // 2, N // 2] = 1.0
     lam = 0.0
     for _ in range(iters):
         z = np.real(apply_adj(apply(x)))

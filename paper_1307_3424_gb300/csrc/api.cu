@@ -10,7 +10,6 @@
 
 namespace wproj {
 
-wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, double e, cudaStream_t s);
 wproj_status power_norm2_impl(wproj_plan *p, int iters, double *out, cudaStream_t s);
 wproj_status solve_bpdn_impl(wproj_plan *p, const float2 *y, double eps, const wproj_dr_params &prm,
                              float *x_out, wproj_solve_info *info, cudaStream_t s);
@@ -223,6 +222,25 @@ wproj_status wproj_build_kernels(wproj_plan *p, const double *uvw, int64_t m, do
   }
   if (out) return wproj_get_csr(p, out);
   return WPROJ_OK;
+}
+
+wproj_status wproj_set_screens(wproj_plan *p, const void *screens, int32_t n_screens, void *stream) {
+  if (!p) return fail(WPROJ_ERR_INVALID_ARG, "null plan");
+  if (n_screens < 0 || (n_screens > 0 && !screens)) return fail(WPROJ_ERR_INVALID_ARG, "set_screens: bad arguments");
+  return set_screens_impl(p, static_cast<const float2 *>(screens), n_screens, as_stream(stream));
+}
+
+wproj_status wproj_build_kernels_dde(wproj_plan *p, const double *uvw, int64_t m, const int32_t *screen_id,
+                                     double e, void *stream) {
+  if (!p) return fail(WPROJ_ERR_INVALID_ARG, "null plan");
+  if (!uvw || !screen_id) return fail(WPROJ_ERR_INVALID_ARG, "null uvw or screen_id");
+  if (m < 1 || m >= (int64_t(1) << 31)) return fail(WPROJ_ERR_INVALID_ARG, "m must be in [1, 2^31)");
+  if (!(e > 0.0 && e <= 1.0)) return fail(WPROJ_ERR_INVALID_ARG, "e must be in (0, 1]");
+  if (p->n_screens < 1) return fail(WPROJ_ERR_INVALID_ARG, "build_kernels_dde: set the screens first");
+  if (p->g.box != p->g.G) return fail(WPROJ_ERR_UNSUPPORTED, "build_kernels_dde: screens need the full box (box = G)");
+  wproj_status st = build_kernels_impl(p, uvw, m, e, as_stream(stream), screen_id);
+  if (st != WPROJ_OK) p->built = false;
+  return st;
 }
 
 wproj_status wproj_get_csr(const wproj_plan *p, wproj_csr *out) {

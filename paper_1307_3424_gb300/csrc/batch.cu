@@ -21,7 +21,6 @@
 #include "plan.h"
 
 namespace wproj {
-wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, double e, cudaStream_t s);
 }
 
 struct wproj_batch {
@@ -212,14 +211,15 @@ __global__ void k_bs_image_scalar(int np, int nbx, const double *__restrict__ pa
   else scal[p * kScal + 3] = v;
 }
 
-// x = z / sqrt(scal[3]) (power iteration), or x = 1/N (start) when scal is null
+// x = z / sqrt(scal[3]) (power iteration), or the unit impulse at the image centre
+// (start) when scal is null
 __global__ void k_bs_scale_image(const BProb *__restrict__ tab, const float *__restrict__ z,
                                  const double *__restrict__ scal, float *__restrict__ x) {
   const BProb P = tab[blockIdx.y];
   const int64_t n = int64_t(P.N) * P.N;
   const float f = scal ? float(1.0 / sqrt(scal[blockIdx.y * kScal + 3])) : 0.f;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-    x[P.img_off + i] = scal ? z[P.img_off + i] * f : 1.0f / P.N;
+    x[P.img_off + i] = scal ? z[P.img_off + i] * f : (i == int64_t(P.N / 2) * P.N + P.N / 2 ? 1.f : 0.f);
 }
 
 // ||Phi||^2 = sqrt(sum) of the last power iteration; mu = 1 / ||Phi||^2
@@ -344,7 +344,7 @@ wproj_status dr_iteration(wproj_batch *b, const float2 *y, int inner, float lamb
   return WPROJ_OK;
 }
 
-// ||Phi_p||^2 of every problem by power iteration from 1/N, then mu_p
+// ||Phi_p||^2 of every problem by power iteration from the centre impulse, then mu_p
 wproj_status power_mu(wproj_batch *b, int iters, cudaStream_t s) {
   const BProb *tab = b->tab.as<BProb>();
   float *x = b->xtmp.as<float>(), *z = b->x.as<float>();

@@ -42,7 +42,7 @@ constexpr int kSelChunk = 8192;          // entries per histogram block
 int64_t degrid_piece(int64_t nnz) { return std::min<int64_t>(16384, std::max<int64_t>(512, nnz / (152 * 64))); }
 int64_t grid_chunk(int64_t nnz) { return std::min<int64_t>(262144, std::max<int64_t>(4096, nnz / (152 * 16))); }
 
-enum : int { ERR_NONFINITE = 1, ERR_BAND = 2, ERR_EMIT = 4 };
+enum : int { ERR_NONFINITE = 1, ERR_BAND = 2, ERR_EMIT = 4, ERR_SCREEN = 8 };
 
 // ---- per-axis tile geometry of a box -----------------------------------------
 // The box covers cells (j0 - S/2 + d) mod G, d in [0, S).  Its touched tiles
@@ -152,6 +152,37 @@ __global__ void k_seg_fill(int64_t m, GridGeom g, const int2 *__restrict__ j0,
   }
 }
 
+// ---- direction-dependent screens ---------------------------------------------------
+
+// every screen id in [0, n)
+__global__ void k_check_sid(int64_t m, const int32_t *__restrict__ sid, int n, int *__restrict__ err) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k < m && (sid[k] < 0 || sid[k] >= n)) atomicOr(err, ERR_SCREEN);
+}
+
+// max |A|^2 of each screen (one block per screen); non-finite samples flag err
+__global__ void __launch_bounds__(256)
+k_screen_max(const float2 *__restrict__ scr, int64_t per, float *__restrict__ max2, int *__restrict__ err) {
+  const float2 *a = scr + int64_t(blockIdx.x) * per;
+  float mx = 0.f;
+  bool bad = false;
+  for (int64_t i = threadIdx.x; i < per; i += blockDim.x) {
+    const float2 v = a[i];
+    if (!isfinite(v.x) || !isfinite(v.y)) bad = true;
+    else mx = fmaxf(mx, v.x * v.x + v.y * v.y);
+  }
+  for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  __shared__ float red[8];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  if (bad) atomicOr(err, ERR_NONFINITE);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int i = 0; i < 8; ++i) t = fmaxf(t, red[i]);
+    max2[blockIdx.x] = t > 0.f ? t : 1.f;   // an all-zero screen keeps the unit scale
+  }
+}
+
 // ---- per-box tables ----------------------------------------------------------------
 
 __global__ void k_coord_tables(int S, double L, int clamp, double *__restrict__ lcoord,
@@ -182,7 +213,8 @@ __global__ void k_box_tables(const int32_t *__restrict__ ids, const double *__re
                              const double *__restrict__ lcoord, float2 *__restrict__ Au,
                              float2 *__restrict__ Av, int8_t *__restrict__ mode,
                              float *__restrict__ wf, double *__restrict__ wd,
-                             SelState *__restrict__ sel) {
+                             SelState *__restrict__ sel, const int32_t *__restrict__ sid,
+                             const float *__restrict__ scr_max2, int32_t *__restrict__ bsid) {
   const int b = blockIdx.x;
   const int k = ids[b];
   const double w = uvw[3 * int64_t(k) + 2];
@@ -213,7 +245,14 @@ __global__ void k_box_tables(const int32_t *__restrict__ ids, const double *__re
     wf[b] = float(w);
     wd[b] = w;
     SelState s = {};
-    s.qscale = 4611686018427387904.0 / (eu * ev);   // 2^62 / E
+    // 2^62 / E: fixed-point energies; with a screen the row energy is at most
+    // E_kb max|A|^2 (Parseval), which keeps the integer sums below 2^62
+    double escale = eu * ev;
+    if (sid) {
+      escale *= double(scr_max2[sid[k]]);
+      bsid[b] = sid[k];
+    }
+    s.qscale = 4611686018427387904.0 / escale;
     sel[b] = s;
   }
   __syncthreads();
@@ -770,7 +809,34 @@ wproj_status make_tile_chunks(int n_tiles, const int64_t *tptr, const int64_t *c
   return WPROJ_OK;
 }
 
-wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, double e, cudaStream_t s) {
+wproj_status set_screens_impl(wproj_plan *p, const float2 *screens, int n, cudaStream_t s) {
+  p->built = false;
+  p->dr_valid = false;
+  p->n_screens = 0;
+  if (n == 0) {
+    p->screens.release();
+    p->screen_max2.release();
+    return WPROJ_OK;
+  }
+  const int64_t per = int64_t(p->g.G) * p->g.G;
+  WPROJ_TRY(p->screens.alloc(sizeof(float2) * per * n));
+  WPROJ_TRY(p->screen_max2.alloc(sizeof(float) * n));
+  WPROJ_CUDA(cudaMemcpyAsync(p->screens.ptr, screens, sizeof(float2) * per * n, cudaMemcpyDefault, s));
+  DevBuf d_err;
+  WPROJ_TRY(d_err.alloc(sizeof(int)));
+  WPROJ_CUDA(cudaMemsetAsync(d_err.ptr, 0, sizeof(int), s));
+  k_screen_max<<<n, 256, 0, s>>>(p->screens.as<float2>(), per, p->screen_max2.as<float>(), d_err.as<int>());
+  WPROJ_CHECK_LAUNCH("screen max");
+  int herr = 0;
+  WPROJ_CUDA(cudaMemcpyAsync(&herr, d_err.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+  WPROJ_CUDA(cudaStreamSynchronize(s));
+  if (herr) return fail(WPROJ_ERR_INVALID_ARG, "set_screens: non-finite screen values");
+  p->n_screens = n;
+  return WPROJ_OK;
+}
+
+wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, double e, cudaStream_t s,
+                                const int32_t *sid) {
   auto t_start = std::chrono::steady_clock::now();
   const GridGeom &g = p->g;
   p->built = false;
@@ -791,11 +857,17 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
                                               d_Sk.as<int32_t>(), d_ntile.as<int32_t>(),
                                               d_sclass.as<int32_t>(), d_err.as<int>());
   WPROJ_CHECK_LAUNCH("row plan");
+  if (sid) {
+    if (p->n_screens < 1 || g.box != g.G) return fail(WPROJ_ERR_UNSUPPORTED, "build_kernels: screens need box = G");
+    k_check_sid<<<ceil_div(m, 256), 256, 0, s>>>(m, sid, p->n_screens, d_err.as<int>());
+    WPROJ_CHECK_LAUNCH("screen ids");
+  }
   int herr = 0;
   WPROJ_CUDA(cudaMemcpyAsync(&herr, d_err.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
   WPROJ_CUDA(cudaStreamSynchronize(s));
   if (herr & ERR_NONFINITE) return fail(WPROJ_ERR_INVALID_ARG, "build_kernels: non-finite (u, v, w)");
   if (herr & ERR_BAND) return fail(WPROJ_ERR_INVALID_ARG, "build_kernels: (u, v) outside [-B, B)");
+  if (herr & ERR_SCREEN) return fail(WPROJ_ERR_INVALID_ARG, "build_kernels: screen id out of range");
 
   // ---- segments (row, touched tile)
   WPROJ_TRY(exclusive_scan_i32_to_i64(d_ntile.as<int32_t>(), d_segbase.as<int64_t>(), m, s));
@@ -846,7 +918,7 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
     max_nb = std::max<int>(max_nb, (int)std::min<int64_t>(std::min<int64_t>(cls_ptr[c + 1] - cls_ptr[c], kMaxBatchBoxes),
                                                             std::max<int64_t>(1, kBuildBatchBytes / per)));
   }
-  DevBuf Kbuf, Au, Av, bmode, bwf, bwd, bsel, hcnt, hq, lcoord, lsq;
+  DevBuf Kbuf, Au, Av, bmode, bwf, bwd, bsel, hcnt, hq, lcoord, lsq, bsid;
   WPROJ_TRY(Kbuf.alloc(std::max<size_t>(kBuildBatchBytes, size_t(p->box_max) * p->box_max * sizeof(float2))));
   WPROJ_TRY(Au.alloc(sizeof(float2) * size_t(max_nb) * p->box_max));
   WPROJ_TRY(Av.alloc(sizeof(float2) * size_t(max_nb) * p->box_max));
@@ -854,6 +926,7 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
   WPROJ_TRY(bwf.alloc(sizeof(float) * max_nb));
   WPROJ_TRY(bwd.alloc(sizeof(double) * max_nb));
   WPROJ_TRY(bsel.alloc(sizeof(SelState) * max_nb));
+  if (sid) WPROJ_TRY(bsid.alloc(sizeof(int32_t) * max_nb));
   WPROJ_TRY(hcnt.alloc(sizeof(unsigned) * kHistBins * size_t(max_nb)));
   WPROJ_TRY(hq.alloc(sizeof(unsigned long long) * kHistBins * size_t(max_nb)));
   WPROJ_TRY(lcoord.alloc(sizeof(double) * p->box_max));
@@ -946,7 +1019,8 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
         const int32_t *ids = d_ids.as<int32_t>() + b0;
         k_box_tables<<<nb, 128, 0, s>>>(ids, uvw, d_delta.as<double2>(), g, S, lcoord.as<double>(),
                                         Au.as<float2>(), Av.as<float2>(), bmode.as<int8_t>(),
-                                        bwf.as<float>(), bwd.as<double>(), bsel.as<SelState>());
+                                        bwf.as<float>(), bwd.as<double>(), bsel.as<SelState>(), sid,
+                                        sid ? p->screen_max2.as<float>() : nullptr, bsid.as<int32_t>());
         WPROJ_CHECK_LAUNCH("box tables");
         BoxBatch bb;
         bb.S = S; bb.nb = nb;
@@ -954,6 +1028,10 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
         bb.mode = bmode.as<int8_t>(); bb.wf = bwf.as<float>(); bb.wd = bwd.as<double>();
         bb.lsq = lsq.as<float>(); bb.lcoord = lcoord.as<double>();
         bb.K = Kbuf.as<float2>();
+        if (sid) {
+          bb.screens = p->screens.as<float2>();
+          bb.bsid = bsid.as<int32_t>();
+        }
         WPROJ_TRY(box_fft(p, bb, s));
         const dim3 hgrid(ceil_div(per, kSelChunk), nb);
         if (phase == 1) {

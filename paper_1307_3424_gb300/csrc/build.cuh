@@ -17,6 +17,10 @@ struct BoxBatch {
   const float *lsq = nullptr;     // [S] l_P^2 (float)
   const double *lcoord = nullptr; // [S] l_P (after clamping)
   float2 *K = nullptr;            // [nb][S][S] kernel values, natural order (offset s at s mod S)
+  // direction-dependent screens (S = G): screens[bsid[b]] multiplies box b's samples;
+  // screen index a holds offset a - S/2 (centred), the box sample P offset P or P - S
+  const float2 *screens = nullptr;
+  const int32_t *bsid = nullptr;
 };
 
 }  // namespace wproj

@@ -11,7 +11,10 @@
 // carried to the next window; a run that crosses a warp boundary is merged by
 // thread 0 in warp order.  Every cell therefore gets a fixed summation order
 // (bit-reproducible), each cell is written once, and the tile's empty cells are
-// zeroed by the same block.
+// zeroed by the same block.  Grids with few tiles split every tile's entries
+// into `parts` contiguous slices, one block each; a block then writes its
+// slice's sums into a private 32 x 32 partial tile and the partials are added
+// per cell in slice order.
 //
 // The copy is built from the tile-ordered segment list by a block per tile:
 // count entries per cell, scan, then place the segments' entries in segment
@@ -121,11 +124,13 @@ __global__ void __launch_bounds__(kCellWarps * 32)
 k_grid_cells(const int64_t *__restrict__ tile_ent, const uint32_t *__restrict__ cell_ent,
              const void *__restrict__ cell_val, const float2 *__restrict__ y,
              int logG, int nT, const int32_t *__restrict__ tile_prob, const BProb *__restrict__ tab,
-             float2 *__restrict__ Xt2) {
+             float2 *__restrict__ Xt2, int parts, float2 *__restrict__ partial) {
   __shared__ int h_cell[kCellWarps], t_cell[kCellWarps], h_closed[kCellWarps];
   __shared__ float2 h_val[kCellWarps], t_val[kCellWarps];
-  int tile = blockIdx.x;
-  const int64_t e0 = tile_ent[tile], e1 = tile_ent[tile + 1];
+  int tile = blockIdx.x / parts;
+  const int part = blockIdx.x % parts;
+  const int64_t te0 = tile_ent[tile], tn = tile_ent[tile + 1] - te0;
+  const int64_t e0 = te0 + tn * part / parts, e1 = te0 + tn * (part + 1) / parts;
   if (tile_prob) {
     const BProb &P = tab[tile_prob[tile]];
     logG = P.logG;
@@ -134,9 +139,13 @@ k_grid_cells(const int64_t *__restrict__ tile_ent, const uint32_t *__restrict__ 
     Xt2 += P.grid_off;
     y += P.vis_off;
   }
-  const int G = 1 << logG;
+  int G = 1 << logG;
   const int tu = tile / nT, tv = tile % nT;
   float2 *out = Xt2 + int64_t(tu * 32) * G + tv * 32;   // cell c at out[(c >> 5) G + (c & 31)]
+  if (parts > 1) {                                      // this slice's partial tile (row stride 32)
+    out = partial + int64_t(blockIdx.x) * 1024;
+    G = 32;
+  }
   for (int c = threadIdx.x; c < 1024; c += blockDim.x) out[int64_t(c >> 5) * G + (c & 31)] = make_float2(0.f, 0.f);
   __syncthreads();
 
@@ -246,6 +255,18 @@ k_grid_cells(const int64_t *__restrict__ tile_ent, const uint32_t *__restrict__ 
   }
 }
 
+// Xt2 cell = sum of the tile's partial tiles in slice order
+__global__ void k_cells_reduce(int n_tiles, int parts, int logG, int nT, const float2 *__restrict__ partial,
+                               float2 *__restrict__ Xt2) {
+  const int tile = blockIdx.x;
+  const int tu = tile / nT, tv = tile % nT;
+  for (int c = threadIdx.x; c < 1024; c += blockDim.x) {
+    float2 acc = make_float2(0.f, 0.f);
+    for (int q = 0; q < parts; ++q) acc = cadd(acc, partial[(int64_t(tile) * parts + q) * 1024 + c]);
+    Xt2[(int64_t(tu * 32 + (c >> 5)) << logG) + tv * 32 + (c & 31)] = acc;
+  }
+}
+
 __global__ void k_tile_ent(int n_tiles, const int64_t *__restrict__ tptr, const int64_t *__restrict__ cum,
                            int64_t n_seg, int64_t nnz, int64_t *__restrict__ tile_ent) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -278,6 +299,16 @@ wproj_status build_cells(wproj_plan *p, const int64_t *tptr, const int64_t *cum,
                                           p->cell_ent.as<uint32_t>(), p->cell_val.as<unsigned char>());
   }
   WPROJ_CHECK_LAUNCH("cell sort");
+  // small grids: split every tile over several blocks so that the SMs fill
+  // (about six blocks per SM, each slice at least 4096 entries)
+  const int64_t want = (152 * 6 + n_tiles - 1) / n_tiles;
+  const int64_t cap = std::max<int64_t>(1, p->nnz / (int64_t(n_tiles) * 4096));
+  p->cell_parts = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(want, cap), 64));
+  if (p->cell_parts > 1) {
+    WPROJ_TRY(p->cell_partial.alloc(sizeof(float2) * size_t(n_tiles) * p->cell_parts * 1024));
+  } else {
+    p->cell_partial.release();
+  }
   return WPROJ_OK;
 }
 
@@ -326,10 +357,12 @@ wproj_status grid_cells(wproj_plan *p, const float2 *y, float2 *Xt2, cudaStream_
     y = p->ytmp.as<float2>();
     p->launches += 1;
   }
-#define GC(VDT)                                                                                            \
-  k_grid_cells<VDT><<<n_tiles, kCellWarps * 32, 0, s>>>(p->tile_ent.as<int64_t>(), p->cell_ent.as<uint32_t>(), \
-                                                        p->cell_val.ptr, y, logG, p->g.nT, nullptr, nullptr,  \
-                                                        Xt2)
+  const int parts = p->cell_parts;
+  float2 *partial = parts > 1 ? p->cell_partial.as<float2>() : nullptr;
+#define GC(VDT)                                                                                                  \
+  k_grid_cells<VDT><<<n_tiles * parts, kCellWarps * 32, 0, s>>>(p->tile_ent.as<int64_t>(),                      \
+                                                                p->cell_ent.as<uint32_t>(), p->cell_val.ptr, y, \
+                                                                logG, p->g.nT, nullptr, nullptr, Xt2, parts, partial)
   switch (p->g.value_dtype) {
     case WPROJ_VAL_F32: GC(WPROJ_VAL_F32); break;
     case WPROJ_VAL_BF16: GC(WPROJ_VAL_BF16); break;
@@ -337,12 +370,17 @@ wproj_status grid_cells(wproj_plan *p, const float2 *y, float2 *Xt2, cudaStream_
   }
 #undef GC
   WPROJ_CHECK_LAUNCH("grid (cells)");
+  if (parts > 1) {
+    k_cells_reduce<<<n_tiles, 256, 0, s>>>(n_tiles, parts, logG, p->g.nT, partial, Xt2);
+    WPROJ_CHECK_LAUNCH("grid (cells) partial tiles");
+    p->launches += 1;
+  }
   return WPROJ_OK;
 }
 
 wproj_status batch_grid_cells(const BatchOps &b, const float2 *y, float2 *Xt2, cudaStream_t s) {
   k_grid_cells<WPROJ_VAL_F32><<<(unsigned)b.n_tiles, kCellWarps * 32, 0, s>>>(
-      b.tile_ent, b.cell_ent, b.cell_val, y, 0, 0, b.tile_prob, b.tab, Xt2);
+      b.tile_ent, b.cell_ent, b.cell_val, y, 0, 0, b.tile_prob, b.tab, Xt2, 1, nullptr);
   WPROJ_CHECK_LAUNCH("batch grid (cells)");
   return WPROJ_OK;
 }

@@ -298,6 +298,11 @@ __device__ __forceinline__ float2 box_value(const BoxBatch &bb, int b, int P, in
     sincospif(2.f * float(fr), &sn, &cs);
     f = cmul(f, make_float2(cs, sn));
   }
+  if (bb.screens) {
+    const int S = bb.S, h = S / 2;
+    const float2 a = bb.screens[(int64_t(bb.bsid[b]) * S + ((P + h) & (S - 1))) * S + ((Q + h) & (S - 1))];
+    f = cmul(f, a);
+  }
   return f;
 }
 
@@ -646,7 +651,7 @@ wproj_status box_fft_separable_impl(wproj_plan *p, const BoxBatch &bb, cudaStrea
 }
 
 wproj_status box_fft(wproj_plan *p, const BoxBatch &bb, cudaStream_t s) {
-  if (p->g.chirp == WPROJ_CHIRP_LINEAR) {   // every box is separable (mode 0)
+  if (p->g.chirp == WPROJ_CHIRP_LINEAR && !bb.screens) {   // every box is separable (mode 0)
 #define CALL(L) box_fft_separable_impl<L>(p, bb, s)
     WPROJ_LOGN_SWITCH(ilog2(bb.S), CALL)
 #undef CALL

@@ -23,7 +23,6 @@
 #include "plan.h"
 
 namespace wproj {
-wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, double e, cudaStream_t s);
 namespace mlpk {
 constexpr int kIn = 3, kH = 256, kOutV = 2048, kOutM = 1024, kOut = kOutV + kOutM, kWin = 32;
 constexpr int64_t oW1 = 0, oB1 = oW1 + kH * kIn, oW2 = oB1 + kH, oB2 = oW2 + kH * kH, oW3 = oB2 + kH,

@@ -133,6 +133,8 @@ struct wproj_plan {
   wproj::DevBuf tile_ent;    // int64[nT*nT+1] first entry of each tile
   wproj::DevBuf cell_ent;    // uint32[nnz]
   wproj::DevBuf cell_val;    // values[nnz]
+  int cell_parts = 1;        // blocks per tile of the cell-major gridding (small grids)
+  wproj::DevBuf cell_partial;    // float2[nT*nT*cell_parts*1024] when cell_parts > 1
   int64_t n_chunks = 0;
   wproj::DevBuf chunk_tile;  // int32[n_chunks]
   wproj::DevBuf chunk_lo;    // int64[n_chunks]  first position in the tile order (seg_meta /
@@ -157,6 +159,9 @@ struct wproj_plan {
   // solver buffers
   wproj::DevBuf s_z, s_x, s_u, s_r, s_scal;   // scal: double scratch for reductions
   wproj::DevBuf s_zi, s_alpha, s_wwork;       // wavelet Psi: Psi z, Psi^T x, transform scratch
+  // direction-dependent screens: float2[n_screens][G][G] (centred) and max |A|^2 of each
+  int n_screens = 0;
+  wproj::DevBuf screens, screen_max2;
 
   // Douglas-Rachford state kept for resume / checkpoint
   bool dr_valid = false;
@@ -200,6 +205,11 @@ wproj_status batch_phi_fwd(int logG, int np, const int32_t *plist, const BProb *
 wproj_status batch_phi_adj(int logG, int np, const int32_t *plist, const BProb *tab, const float2 *Xt2,
                            const float *inv_a, float2 *inter, float *x_re, const float *z, int mode,
                            const float2 *tw, cudaStream_t s);
+
+// build.cu: G from (u, v, w); sid (device, nullable): a screen per row (needs box = G)
+wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, double e, cudaStream_t s,
+                                const int32_t *sid = nullptr);
+wproj_status set_screens_impl(wproj_plan *p, const float2 *screens, int n, cudaStream_t s);
 
 // wavelet.cu: the Daubechies basis; work holds N*N/2 floats
 wproj_status daubechies_taps_impl(int p, double *h_out);

@@ -130,6 +130,12 @@ __global__ void k_normalise(int64_t n, const float *__restrict__ z, const double
     x[i] = z[i] * f;
 }
 
+// the unit impulse at flat index `at`
+__global__ void k_impulse(int64_t n, float *__restrict__ x, int64_t at) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    x[i] = i == at ? 1.f : 0.f;
+}
+
 __global__ void k_fill(int64_t n, float *__restrict__ x, float v) {
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) x[i] = v;
 }
@@ -148,7 +154,8 @@ wproj_status ensure_solver_buffers(wproj_plan *p) {
 
 }  // namespace
 
-// ||Phi||^2 by power iteration on Re Phi^H Phi from the constant image 1/N.
+// ||Phi||^2 by power iteration on Re Phi^H Phi from the unit impulse at the image
+// centre (flat spectrum: no row of Phi is orthogonal to it).
 wproj_status power_norm2_impl(wproj_plan *p, int iters, double *out, cudaStream_t s) {
   WPROJ_TRY(ensure_solver_buffers(p));
   const int64_t n = int64_t(p->g.N) * p->g.N;
@@ -157,8 +164,8 @@ wproj_status power_norm2_impl(wproj_plan *p, int iters, double *out, cudaStream_
   float2 *r = p->s_r.as<float2>();
   double *scal = p->s_scal.as<double>();
   double *part = scal + 8;
-  k_fill<<<grid_for(n), kRedThreads, 0, s>>>(n, x, 1.0f / p->g.N);
-  WPROJ_CHECK_LAUNCH("fill");
+  k_impulse<<<grid_for(n), kRedThreads, 0, s>>>(n, x, int64_t(p->g.N / 2) * p->g.N + p->g.N / 2);
+  WPROJ_CHECK_LAUNCH("power iteration start");
   p->launches += 1;
   for (int it = 0; it < iters; ++it) {
     WPROJ_TRY(apply_phi(p, x, nullptr, r, s));
@@ -184,6 +191,8 @@ wproj_status solve_bpdn_impl(wproj_plan *p, const float2 *y, double eps, const w
   double phi_norm2 = prm.phi_norm2;
   if (!(phi_norm2 > 0) && resume) phi_norm2 = p->dr_phi_norm2;
   if (!(phi_norm2 > 0)) WPROJ_TRY(power_norm2_impl(p, prm.power_iters, &phi_norm2, s));
+  if (!(phi_norm2 > 0) || !isfinite(phi_norm2))
+    return fail(WPROJ_ERR_INVALID_ARG, "solve_bpdn: ||Phi||^2 is zero or not finite");
   const double mu = 1.0 / phi_norm2;
   const int64_t n = int64_t(p->g.N) * p->g.N;
   const int64_t m = p->m;

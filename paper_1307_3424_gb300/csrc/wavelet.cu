@@ -23,10 +23,11 @@
 namespace wproj {
 
 constexpr int kMaxTaps = 2 * WPROJ_DAUB_MAX_P;
-constexpr int kWT = 16;                       // analysis output tile (per sub-band); synthesis input tile
+constexpr int kWT = 32;                       // analysis output tile (per sub-band); synthesis input tile
 constexpr int kWIn = 2 * kWT + kMaxTaps - 2;  // staged input side of an analysis tile
 constexpr int kWSyn = kWT + kMaxTaps / 2 - 1; // staged sub-band side of a synthesis tile
 constexpr int kWThreads = 256;
+constexpr int kWWarps = kWThreads / 32;
 
 struct Taps {
   float h[kMaxTaps];
@@ -149,94 +150,117 @@ __device__ __forceinline__ int wrap(int i, int n) {
   return i < 0 ? i + n : i;
 }
 
+// i in [0, 2n) when n >= the staged span (one subtraction), else a full wrap
+__device__ __forceinline__ int wrap_up(int i, int n, bool big) {
+  if (big) return i >= n ? i - n : i;
+  return i % n;
+}
+
 // One analysis level: src (n x n, row stride lds) -> the four sub-bands; the
 // low-low band to ll (row stride ldl), the three others into the Mallat blocks of
-// coef (row stride ldc).
+// coef (row stride ldc).  A CTA makes a 32 x 32 tile of each band from the
+// (64 + L - 2)^2 input region, wrapped periodically.
 __global__ void __launch_bounds__(kWThreads)
 k_dwt_level(const float *__restrict__ src, int lds, int n, const Taps t, float *__restrict__ ll, int ldl,
             float *__restrict__ coef, int ldc) {
-  __shared__ float in[kWIn][kWIn + 1];
-  __shared__ float lo[kWIn][kWT + 1], hi[kWIn][kWT + 1];
+  __shared__ float in[kWIn][kWIn];
+  __shared__ float lo[kWIn][kWT], hi[kWIn][kWT];
   const int h = n / 2, L = t.len;
   const int i0 = blockIdx.y * kWT, c0 = blockIdx.x * kWT;
   const int span = 2 * kWT + L - 2;
-  for (int e = threadIdx.x; e < span * span; e += kWThreads) {
-    const int r = e / span, c = e % span;
-    in[r][c] = src[int64_t(wrap(2 * i0 + r, n)) * lds + wrap(2 * c0 + c, n)];
+  const bool big = n >= span;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int r = wid; r < span; r += kWWarps) {
+    const float *row = src + int64_t(wrap_up(2 * i0 + r, n, big)) * lds;
+    for (int c = lane; c < span; c += 32) in[r][c] = row[wrap_up(2 * c0 + c, n, big)];
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < span * kWT; e += kWThreads) {      // fast axis
-    const int r = e / kWT, c = e % kWT;
+  for (int r = wid; r < span; r += kWWarps) {      // fast axis: lane = output column
     float a = 0.f, d = 0.f;
     for (int k = 0; k < L; ++k) {
-      const float v = in[r][2 * c + k];
+      const float v = in[r][2 * lane + k];
       a = fmaf(t.h[k], v, a);
       d = fmaf(t.g[k], v, d);
     }
-    lo[r][c] = a;
-    hi[r][c] = d;
+    lo[r][lane] = a;
+    hi[r][lane] = d;
   }
   __syncthreads();
-  const int i = threadIdx.x / kWT, c = threadIdx.x % kWT;        // slow axis
-  float s_ll = 0.f, s_lh = 0.f, s_hl = 0.f, s_hh = 0.f;
-  for (int k = 0; k < L; ++k) {
-    const float vl = lo[2 * i + k][c], vh = hi[2 * i + k][c];
-    s_ll = fmaf(t.h[k], vl, s_ll);
-    s_lh = fmaf(t.h[k], vh, s_lh);
-    s_hl = fmaf(t.g[k], vl, s_hl);
-    s_hh = fmaf(t.g[k], vh, s_hh);
-  }
-  const int gi = i0 + i, gc = c0 + c;
-  if (gi < h && gc < h) {
-    ll[int64_t(gi) * ldl + gc] = s_ll;
-    coef[int64_t(gi) * ldc + h + gc] = s_lh;         // low slow, high fast
-    coef[int64_t(h + gi) * ldc + gc] = s_hl;         // high slow, low fast
-    coef[int64_t(h + gi) * ldc + h + gc] = s_hh;
+  const int gc = c0 + lane;
+  for (int i = wid; i < kWT; i += kWWarps) {         // slow axis
+    float s_ll = 0.f, s_lh = 0.f, s_hl = 0.f, s_hh = 0.f;
+    for (int k = 0; k < L; ++k) {
+      const float vl = lo[2 * i + k][lane], vh = hi[2 * i + k][lane];
+      s_ll = fmaf(t.h[k], vl, s_ll);
+      s_lh = fmaf(t.h[k], vh, s_lh);
+      s_hl = fmaf(t.g[k], vl, s_hl);
+      s_hh = fmaf(t.g[k], vh, s_hh);
+    }
+    const int gi = i0 + i;
+    if (gi < h && gc < h) {
+      ll[int64_t(gi) * ldl + gc] = s_ll;
+      coef[int64_t(gi) * ldc + h + gc] = s_lh;         // low slow, high fast
+      coef[int64_t(h + gi) * ldc + gc] = s_hl;         // high slow, low fast
+      coef[int64_t(h + gi) * ldc + h + gc] = s_hh;
+    }
   }
 }
 
 // One synthesis level: the low-low band ll (row stride ldl) and the three other
-// bands of coef (row stride ldc) -> dst (n x n, row stride ldd).
+// bands of coef (row stride ldc) -> dst (n x n, row stride ldd).  A CTA makes a
+// 64 x 64 output tile from (32 + L/2 - 1)^2 samples of each band.
 __global__ void __launch_bounds__(kWThreads)
 k_idwt_level(const float *__restrict__ ll, int ldl, const float *__restrict__ coef, int ldc, int n, const Taps t,
              float *__restrict__ dst, int ldd) {
-  __shared__ float sb[4][kWSyn][kWSyn + 1];
-  __shared__ float lo[kWSyn][2 * kWT + 1], hi[kWSyn][2 * kWT + 1];
+  __shared__ float sb[4][kWSyn][kWSyn];
+  __shared__ float lo[kWSyn][2 * kWT], hi[kWSyn][2 * kWT];
   const int h = n / 2, L = t.len;
   const int j10 = blockIdx.y * 2 * kWT, j20 = blockIdx.x * 2 * kWT;
   const int off = L / 2 - 1;                      // staged index = band index - (j0/2 - off)
   const int span = kWT + off;
   const int b1 = j10 / 2 - off, b2 = j20 / 2 - off;
-  for (int e = threadIdx.x; e < span * span; e += kWThreads) {
-    const int r = e / span, c = e % span;
-    const int gi = wrap(b1 + r, h), gc = wrap(b2 + c, h);
-    sb[0][r][c] = ll[int64_t(gi) * ldl + gc];
-    sb[1][r][c] = coef[int64_t(gi) * ldc + h + gc];
-    sb[2][r][c] = coef[int64_t(h + gi) * ldc + gc];
-    sb[3][r][c] = coef[int64_t(h + gi) * ldc + h + gc];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int r = wid; r < span; r += kWWarps) {
+    const int gi = wrap(b1 + r, h);
+    const float *lrow = ll + int64_t(gi) * ldl;
+    const float *crow = coef + int64_t(gi) * ldc, *crow2 = coef + int64_t(h + gi) * ldc;
+    for (int c = lane; c < span; c += 32) {
+      const int gc = wrap(b2 + c, h);
+      sb[0][r][c] = lrow[gc];
+      sb[1][r][c] = crow[h + gc];
+      sb[2][r][c] = crow2[gc];
+      sb[3][r][c] = crow2[h + gc];
+    }
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < span * 2 * kWT; e += kWThreads) {   // fast axis
-    const int r = e / (2 * kWT), jj = e % (2 * kWT);
-    float a = 0.f, d = 0.f;
-    for (int k = jj & 1; k < L; k += 2) {
-      const int q = (jj - k) / 2 + off;
-      a = fmaf(t.h[k], sb[0][r][q], fmaf(t.g[k], sb[1][r][q], a));
-      d = fmaf(t.h[k], sb[2][r][q], fmaf(t.g[k], sb[3][r][q], d));
+  for (int r = wid; r < span; r += kWWarps) {     // fast axis: lane and lane + 32 = output columns
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int jj = lane + 32 * half;
+      float a = 0.f, d = 0.f;
+      for (int k = jj & 1; k < L; k += 2) {
+        const int q = (jj - k) / 2 + off;
+        a = fmaf(t.h[k], sb[0][r][q], fmaf(t.g[k], sb[1][r][q], a));
+        d = fmaf(t.h[k], sb[2][r][q], fmaf(t.g[k], sb[3][r][q], d));
+      }
+      lo[r][jj] = a;
+      hi[r][jj] = d;
     }
-    lo[r][jj] = a;
-    hi[r][jj] = d;
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < 4 * kWT * kWT; e += kWThreads) {    // slow axis
-    const int ii = e / (2 * kWT), jj = e % (2 * kWT);
-    float v = 0.f;
-    for (int k = ii & 1; k < L; k += 2) {
-      const int q = (ii - k) / 2 + off;
-      v = fmaf(t.h[k], lo[q][jj], fmaf(t.g[k], hi[q][jj], v));
+  for (int ii = wid; ii < 2 * kWT; ii += kWWarps) {    // slow axis
+    const int g1 = j10 + ii;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int jj = lane + 32 * half;
+      float v = 0.f;
+      for (int k = ii & 1; k < L; k += 2) {
+        const int q = (ii - k) / 2 + off;
+        v = fmaf(t.h[k], lo[q][jj], fmaf(t.g[k], hi[q][jj], v));
+      }
+      const int g2 = j20 + jj;
+      if (g1 < n && g2 < n) dst[int64_t(g1) * ldd + g2] = v;
     }
-    const int g1 = j10 + ii, g2 = j20 + jj;
-    if (g1 < n && g2 < n) dst[int64_t(g1) * ldd + g2] = v;
   }
 }
 

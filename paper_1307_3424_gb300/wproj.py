@@ -33,7 +33,7 @@ EXPORTED = [
     "wproj_batch_get_info", "wproj_gemm_bf16", "wproj_mlp_num_params", "wproj_mlp_create",
     "wproj_mlp_destroy", "wproj_mlp_set_params", "wproj_mlp_get_params", "wproj_mlp_targets",
     "wproj_mlp_forward", "wproj_mlp_gradients", "wproj_mlp_train", "wproj_build_kernels_learned",
-    "wproj_daubechies_taps", "wproj_dwt2", "wproj_idwt2",
+    "wproj_daubechies_taps", "wproj_dwt2", "wproj_idwt2", "wproj_set_screens", "wproj_build_kernels_dde",
 ]
 
 
@@ -145,6 +145,8 @@ def lib() -> ctypes.CDLL:
         "wproj_batch_get_info": [vp, P(BatchInfo)],
         "wproj_gemm_bf16": [i32, i32, i32, vp, vp, vp, vp, i32, vp],
         "wproj_daubechies_taps": [i32, P(dbl)],
+        "wproj_set_screens": [vp, vp, i32, vp],
+        "wproj_build_kernels_dde": [vp, vp, i64, vp, dbl, vp],
         "wproj_dwt2": [i32, i32, i32, vp, vp, vp, vp],
         "wproj_idwt2": [i32, i32, i32, vp, vp, vp, vp],
         "wproj_mlp_create": [P(vp)],
@@ -298,14 +300,36 @@ class Plan:
         return self._h
 
     # ---- Part I
-    def build_kernels(self, uvw: torch.Tensor, e: float, stream=None) -> CSR:
+    def build_kernels(self, uvw: torch.Tensor, e: float, screen_id: torch.Tensor | None = None,
+                      stream=None) -> CSR:
+        """G for the visibilities uvw (M, 3); screen_id (M int32 on the device)
+        attaches the screen set by set_screens to every row."""
         if uvw.dtype != torch.float64 or uvw.dim() != 2 or uvw.shape[1] != 3:
             raise WprojError(ERR_INVALID_ARG, "uvw must be an (M, 3) float64 tensor")
         out = CSR()
-        _check(lib().wproj_build_kernels(self._h, _ptr(uvw), uvw.shape[0], float(e), _stream(stream),
-                                         ctypes.byref(out)))
+        if screen_id is None:
+            _check(lib().wproj_build_kernels(self._h, _ptr(uvw), uvw.shape[0], float(e), _stream(stream),
+                                             ctypes.byref(out)))
+        else:
+            if screen_id.dtype != torch.int32 or screen_id.numel() != uvw.shape[0] or not screen_id.is_cuda:
+                raise WprojError(ERR_INVALID_ARG, "screen_id must be an int32 device tensor of M ids")
+            _check(lib().wproj_build_kernels_dde(self._h, _ptr(uvw), uvw.shape[0], _ptr(screen_id.contiguous()),
+                                                 float(e), _stream(stream)))
+            _check(lib().wproj_get_csr(self._h, ctypes.byref(out)))
         self.m = int(out.m)
         return out
+
+    def set_screens(self, screens: torch.Tensor | None, stream=None):
+        """Direction-dependent screens, complex64 (n, G, G), centred (index a at
+        offset a - G/2); None drops them."""
+        if screens is None:
+            _check(lib().wproj_set_screens(self._h, None, 0, _stream(stream)))
+            return
+        G = 2 * self.n
+        if screens.dtype != torch.complex64 or screens.dim() != 3 or tuple(screens.shape[1:]) != (G, G):
+            raise WprojError(ERR_INVALID_ARG, f"screens must be complex64 (n, {G}, {G})")
+        screens = screens.contiguous()
+        _check(lib().wproj_set_screens(self._h, _ptr(screens), screens.shape[0], _stream(stream)))
 
     def build_kernels_learned(self, net: "MLP", uvw: torch.Tensor, e: float, rel_l2_max: float = 1e-3,
                               stream=None):

@@ -106,7 +106,7 @@ def test_dr_with_db8_matches_oracle(wp):
         return W.dwt2(np.real(O.phi_adj(geo, Gm, r)), levels, 8)
 
     # Psi is orthonormal, so ||Phi Psi|| = ||Phi||: both sides take the power
-    # iteration of Phi alone (from the constant image)
+    # iteration of Phi alone (from the centre impulse)
     n2 = O.power_norm2(lambda v: O.phi(geo, Gm, v), lambda r: np.real(O.phi_adj(geo, Gm, r)), wl.N, 100)
     a_or, info_or = O.solve_bpdn(ap, aa, y, eps, wl.N, iters, inner_iters=wl.inner_iters, phi_norm2=n2)
     x_or = W.idwt2(a_or, levels, 8)
