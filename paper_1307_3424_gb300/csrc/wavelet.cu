@@ -150,6 +150,14 @@ __device__ __forceinline__ int wrap(int i, int n) {
   return i < 0 ? i + n : i;
 }
 
+// global -> shared copy of one float without a register round trip, so that all
+// of a CTA's staging copies are in flight together
+__device__ __forceinline__ void cp_async4(float *smem, const float *gmem) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // i in [0, 2n) when n >= the staged span (one subtraction), else a full wrap
 __device__ __forceinline__ int wrap_up(int i, int n, bool big) {
   if (big) return i >= n ? i - n : i;
@@ -159,107 +167,151 @@ __device__ __forceinline__ int wrap_up(int i, int n, bool big) {
 // One analysis level: src (n x n, row stride lds) -> the four sub-bands; the
 // low-low band to ll (row stride ldl), the three others into the Mallat blocks of
 // coef (row stride ldc).  A CTA makes a 32 x 32 tile of each band from the
-// (64 + L - 2)^2 input region, wrapped periodically.
+// (64 + L - 2)^2 input region, wrapped periodically.  Each filtering task keeps
+// the inputs of 8 consecutive outputs in registers (two shared-memory loads per
+// output instead of L), the tap count L = 2p a compile-time constant.
+template <int L>
 __global__ void __launch_bounds__(kWThreads)
 k_dwt_level(const float *__restrict__ src, int lds, int n, const Taps t, float *__restrict__ ll, int ldl,
             float *__restrict__ coef, int ldc) {
-  __shared__ float in[kWIn][kWIn];
-  __shared__ float lo[kWIn][kWT], hi[kWIn][kWT];
-  const int h = n / 2, L = t.len;
+  constexpr int span = 2 * kWT + L - 2;
+  constexpr int SEG = 8, NW = 2 * SEG + L - 2;      // outputs per task, inputs per task
+  __shared__ float in[span][span + 1];
+  __shared__ float lo[span][kWT + 1], hi[span][kWT + 1];
+  const int h = n / 2;
   const int i0 = blockIdx.y * kWT, c0 = blockIdx.x * kWT;
-  const int span = 2 * kWT + L - 2;
   const bool big = n >= span;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  float hk[L], gk[L];
+#pragma unroll
+  for (int k = 0; k < L; ++k) { hk[k] = t.h[k]; gk[k] = t.g[k]; }
   for (int r = wid; r < span; r += kWWarps) {
     const float *row = src + int64_t(wrap_up(2 * i0 + r, n, big)) * lds;
-    for (int c = lane; c < span; c += 32) in[r][c] = row[wrap_up(2 * c0 + c, n, big)];
+    for (int c = lane; c < span; c += 32) cp_async4(&in[r][c], row + wrap_up(2 * c0 + c, n, big));
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  for (int task = threadIdx.x; task < span * (kWT / SEG); task += kWThreads) {   // fast axis
+    const int r = task / (kWT / SEG), q = task % (kWT / SEG);
+    float v[NW];
+#pragma unroll
+    for (int j = 0; j < NW; ++j) v[j] = in[r][2 * SEG * q + j];
+#pragma unroll
+    for (int o = 0; o < SEG; ++o) {
+      float a = 0.f, d = 0.f;
+#pragma unroll
+      for (int k = 0; k < L; ++k) {
+        a = fmaf(hk[k], v[2 * o + k], a);
+        d = fmaf(gk[k], v[2 * o + k], d);
+      }
+      lo[r][SEG * q + o] = a;
+      hi[r][SEG * q + o] = d;
+    }
   }
   __syncthreads();
-  for (int r = wid; r < span; r += kWWarps) {      // fast axis: lane = output column
-    float a = 0.f, d = 0.f;
-    for (int k = 0; k < L; ++k) {
-      const float v = in[r][2 * lane + k];
-      a = fmaf(t.h[k], v, a);
-      d = fmaf(t.g[k], v, d);
-    }
-    lo[r][lane] = a;
-    hi[r][lane] = d;
-  }
-  __syncthreads();
-  const int gc = c0 + lane;
-  for (int i = wid; i < kWT; i += kWWarps) {         // slow axis
-    float s_ll = 0.f, s_lh = 0.f, s_hl = 0.f, s_hh = 0.f;
-    for (int k = 0; k < L; ++k) {
-      const float vl = lo[2 * i + k][lane], vh = hi[2 * i + k][lane];
-      s_ll = fmaf(t.h[k], vl, s_ll);
-      s_lh = fmaf(t.h[k], vh, s_lh);
-      s_hl = fmaf(t.g[k], vl, s_hl);
-      s_hh = fmaf(t.g[k], vh, s_hh);
-    }
-    const int gi = i0 + i;
-    if (gi < h && gc < h) {
-      ll[int64_t(gi) * ldl + gc] = s_ll;
-      coef[int64_t(gi) * ldc + h + gc] = s_lh;         // low slow, high fast
-      coef[int64_t(h + gi) * ldc + gc] = s_hl;         // high slow, low fast
-      coef[int64_t(h + gi) * ldc + h + gc] = s_hh;
+  {                                                  // slow axis: one task per thread
+    const int c = threadIdx.x & 31, sel = (threadIdx.x >> 5) & 1, q = threadIdx.x >> 6;
+    float v[NW];
+#pragma unroll
+    for (int j = 0; j < NW; ++j) v[j] = sel ? hi[2 * SEG * q + j][c] : lo[2 * SEG * q + j][c];
+    const int gc = c0 + c;
+#pragma unroll
+    for (int o = 0; o < SEG; ++o) {
+      float a = 0.f, d = 0.f;
+#pragma unroll
+      for (int k = 0; k < L; ++k) {
+        a = fmaf(hk[k], v[2 * o + k], a);
+        d = fmaf(gk[k], v[2 * o + k], d);
+      }
+      const int gi = i0 + SEG * q + o;
+      if (gi < h && gc < h) {
+        if (sel == 0) {
+          ll[int64_t(gi) * ldl + gc] = a;                  // low slow, low fast
+          coef[int64_t(h + gi) * ldc + gc] = d;            // high slow, low fast
+        } else {
+          coef[int64_t(gi) * ldc + h + gc] = a;            // low slow, high fast
+          coef[int64_t(h + gi) * ldc + h + gc] = d;        // high slow, high fast
+        }
+      }
     }
   }
 }
 
 // One synthesis level: the low-low band ll (row stride ldl) and the three other
 // bands of coef (row stride ldc) -> dst (n x n, row stride ldd).  A CTA makes a
-// 64 x 64 output tile from (32 + L/2 - 1)^2 samples of each band.
+// 64 x 64 output tile from (32 + L/2 - 1)^2 samples of each band; each task keeps
+// the band samples of 16 consecutive outputs in registers.
+template <int L>
 __global__ void __launch_bounds__(kWThreads)
 k_idwt_level(const float *__restrict__ ll, int ldl, const float *__restrict__ coef, int ldc, int n, const Taps t,
              float *__restrict__ dst, int ldd) {
-  __shared__ float sb[4][kWSyn][kWSyn];
-  __shared__ float lo[kWSyn][2 * kWT], hi[kWSyn][2 * kWT];
-  const int h = n / 2, L = t.len;
+  constexpr int off = L / 2 - 1;                   // staged index = band index - (j0/2 - off)
+  constexpr int span = kWT + off;
+  constexpr int SEG = 16, NW = SEG / 2 + off;      // outputs per task, band samples per task
+  __shared__ float sb[4][span][span + 1];
+  __shared__ float lo[span][2 * kWT + 1], hi[span][2 * kWT + 1];
+  const int h = n / 2;
   const int j10 = blockIdx.y * 2 * kWT, j20 = blockIdx.x * 2 * kWT;
-  const int off = L / 2 - 1;                      // staged index = band index - (j0/2 - off)
-  const int span = kWT + off;
   const int b1 = j10 / 2 - off, b2 = j20 / 2 - off;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  float hk[L], gk[L];
+#pragma unroll
+  for (int k = 0; k < L; ++k) { hk[k] = t.h[k]; gk[k] = t.g[k]; }
   for (int r = wid; r < span; r += kWWarps) {
     const int gi = wrap(b1 + r, h);
     const float *lrow = ll + int64_t(gi) * ldl;
     const float *crow = coef + int64_t(gi) * ldc, *crow2 = coef + int64_t(h + gi) * ldc;
     for (int c = lane; c < span; c += 32) {
       const int gc = wrap(b2 + c, h);
-      sb[0][r][c] = lrow[gc];
-      sb[1][r][c] = crow[h + gc];
-      sb[2][r][c] = crow2[gc];
-      sb[3][r][c] = crow2[h + gc];
+      cp_async4(&sb[0][r][c], lrow + gc);
+      cp_async4(&sb[1][r][c], crow + h + gc);
+      cp_async4(&sb[2][r][c], crow2 + gc);
+      cp_async4(&sb[3][r][c], crow2 + h + gc);
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  // fast axis: task (band row r, pair: 0 = (LL, LH) -> lo, 1 = (HL, HH) -> hi, segment q)
+  for (int task = threadIdx.x; task < span * 2 * (2 * kWT / SEG); task += kWThreads) {
+    const int q = task % (2 * kWT / SEG), pr = (task / (2 * kWT / SEG)) & 1, r = task / (4 * kWT / SEG);
+    float a[NW], d[NW];
+#pragma unroll
+    for (int j = 0; j < NW; ++j) {
+      a[j] = sb[2 * pr][r][SEG / 2 * q + j];
+      d[j] = sb[2 * pr + 1][r][SEG / 2 * q + j];
+    }
+    float *outr = pr ? hi[r] : lo[r];
+#pragma unroll
+    for (int o = 0; o < SEG; ++o) {
+      float x = 0.f;
+#pragma unroll
+      for (int k = o & 1; k < L; k += 2) {
+        const int idx = (o - k) / 2 + off;            // compile-time after unrolling
+        x = fmaf(hk[k], a[idx], fmaf(gk[k], d[idx], x));
+      }
+      outr[SEG * q + o] = x;
     }
   }
   __syncthreads();
-  for (int r = wid; r < span; r += kWWarps) {     // fast axis: lane and lane + 32 = output columns
+  {                                                  // slow axis: task (column jj, segment q)
+    const int jj = threadIdx.x & (2 * kWT - 1), q = threadIdx.x / (2 * kWT);
+    float a[NW], d[NW];
 #pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const int jj = lane + 32 * half;
-      float a = 0.f, d = 0.f;
-      for (int k = jj & 1; k < L; k += 2) {
-        const int q = (jj - k) / 2 + off;
-        a = fmaf(t.h[k], sb[0][r][q], fmaf(t.g[k], sb[1][r][q], a));
-        d = fmaf(t.h[k], sb[2][r][q], fmaf(t.g[k], sb[3][r][q], d));
-      }
-      lo[r][jj] = a;
-      hi[r][jj] = d;
+    for (int j = 0; j < NW; ++j) {
+      a[j] = lo[SEG / 2 * q + j][jj];
+      d[j] = hi[SEG / 2 * q + j][jj];
     }
-  }
-  __syncthreads();
-  for (int ii = wid; ii < 2 * kWT; ii += kWWarps) {    // slow axis
-    const int g1 = j10 + ii;
+    const int g2 = j20 + jj;
 #pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const int jj = lane + 32 * half;
-      float v = 0.f;
-      for (int k = ii & 1; k < L; k += 2) {
-        const int q = (ii - k) / 2 + off;
-        v = fmaf(t.h[k], lo[q][jj], fmaf(t.g[k], hi[q][jj], v));
+    for (int o = 0; o < SEG; ++o) {
+      float x = 0.f;
+#pragma unroll
+      for (int k = o & 1; k < L; k += 2) {
+        const int idx = (o - k) / 2 + off;
+        x = fmaf(hk[k], a[idx], fmaf(gk[k], d[idx], x));
       }
-      const int g2 = j20 + jj;
-      if (g1 < n && g2 < n) dst[int64_t(g1) * ldd + g2] = v;
+      const int g1 = j10 + SEG * q + o;
+      if (g1 < n && g2 < n) dst[int64_t(g1) * ldd + g2] = x;
     }
   }
 }
@@ -289,7 +341,14 @@ wproj_status dwt2_impl(int N, int levels, int p, const float *x, float *alpha, f
     float *ll = last ? alpha : ping[lv & 1];
     const int ldl = last ? N : h;
     const dim3 grid(ceil_div(h, kWT), ceil_div(h, kWT));
-    k_dwt_level<<<grid, kWThreads, 0, s>>>(src, lds, n, t, ll, ldl, alpha, N);
+    switch (t.len) {
+#define DWT_CASE(L) \
+  case L: k_dwt_level<L><<<grid, kWThreads, 0, s>>>(src, lds, n, t, ll, ldl, alpha, N); break;
+      DWT_CASE(2) DWT_CASE(4) DWT_CASE(6) DWT_CASE(8) DWT_CASE(10)
+      DWT_CASE(12) DWT_CASE(14) DWT_CASE(16) DWT_CASE(18) DWT_CASE(20)
+#undef DWT_CASE
+      default: return fail(WPROJ_ERR_INVALID_ARG, "Daubechies order out of range");
+    }
     WPROJ_CHECK_LAUNCH("wavelet analysis level");
     src = ll;
     lds = ldl;
@@ -315,7 +374,14 @@ wproj_status idwt2_impl(int N, int levels, int p, const float *alpha, float *x, 
     float *dst = last ? x : ping[lv & 1];
     const int ldd = last ? N : n;
     const dim3 grid(ceil_div(n, 2 * kWT), ceil_div(n, 2 * kWT));
-    k_idwt_level<<<grid, kWThreads, 0, s>>>(ll, ldl, alpha, N, n, t, dst, ldd);
+    switch (t.len) {
+#define IDWT_CASE(L) \
+  case L: k_idwt_level<L><<<grid, kWThreads, 0, s>>>(ll, ldl, alpha, N, n, t, dst, ldd); break;
+      IDWT_CASE(2) IDWT_CASE(4) IDWT_CASE(6) IDWT_CASE(8) IDWT_CASE(10)
+      IDWT_CASE(12) IDWT_CASE(14) IDWT_CASE(16) IDWT_CASE(18) IDWT_CASE(20)
+#undef IDWT_CASE
+      default: return fail(WPROJ_ERR_INVALID_ARG, "Daubechies order out of range");
+    }
     WPROJ_CHECK_LAUNCH("wavelet synthesis level");
     ll = dst;
     ldl = ldd;
