@@ -96,9 +96,10 @@ typedef struct {
  *                entries in it (rows ascending), one record, 16-byte aligned:
  *                  int32 row, int32 count, int32 segment id, int32 0   (16 B)
  *                  32 uint32 mask words, bit l of word r = cell (r, l) stored
+ *                  32 uint16 prefixes: entries stored in tile rows 0 .. r-1
  *                  count values in row-major cell order, zero-padded to 16 B
- *                (128 B of mask per segment instead of 4 B per entry, and each
- *                tile's records contiguous for streaming).
+ *                (192 B of mask and prefixes per segment instead of 4 B per
+ *                entry, and each tile's records contiguous for streaming).
  * AUTO picks TILE_MASK when segments average >= 256 entries (dense rows), COLUMNS
  * otherwise.  wproj_csr_rows exports any rows in CSR order from either format. */
 typedef enum { WPROJ_INDEX_AUTO = 0, WPROJ_INDEX_COLUMNS = 1, WPROJ_INDEX_TILE_MASK = 2 } wproj_index_format;

@@ -627,7 +627,10 @@ k_emit(const float2 *__restrict__ K, int S, const int32_t *__restrict__ ids,
       }
     }
     if (rec) {
-      if (w == 0) reinterpret_cast<uint32_t *>(rp + kRecHeader)[lane] = selw[lane];
+      if (w == 0) {
+        reinterpret_cast<uint32_t *>(rp + kRecHeader)[lane] = selw[lane];
+        reinterpret_cast<uint16_t *>(rp + kRecPrefix)[lane] = uint16_t(selpre[lane]);
+      }
       if (threadIdx.x == 0) *reinterpret_cast<int4 *>(rp) = make_int4(k, cnt, int(sid), 0);
     }
     __syncthreads();

@@ -15,9 +15,11 @@ namespace wproj {
 constexpr int kTile = 32;          // side of the grid tiles used for gridding and CSR order
 constexpr double kSelectMargin = 1e-5;   // extra kept energy fraction (covers FP32 error)
 // tile-stream records (TILE_MASK format): 16-byte header (row, count, segment
-// id, 0), 32 mask words, then the values from this byte offset on
+// id, 0), 32 mask words, 32 uint16 row prefixes (entries before each tile row),
+// then the values from kRecValues on
 constexpr int kRecHeader = 16;
-constexpr int kRecValues = kRecHeader + 32 * 4;
+constexpr int kRecPrefix = kRecHeader + 32 * 4;
+constexpr int kRecValues = kRecPrefix + 32 * 2;
 // consumer warps of the tile-stream kernels: the degridding leaves one partial
 // sum per (record, warp)
 constexpr int kStreamWarps = 4;

@@ -136,10 +136,6 @@ __global__ void k_impulse(int64_t n, float *__restrict__ x, int64_t at) {
     x[i] = i == at ? 1.f : 0.f;
 }
 
-__global__ void k_fill(int64_t n, float *__restrict__ x, float v) {
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) x[i] = v;
-}
-
 int grid_for(int64_t n) { return (int)std::min<int64_t>(kRedBlocks, std::max<int64_t>(1, ceil_div(n, kRedThreads))); }
 
 wproj_status ensure_solver_buffers(wproj_plan *p) {

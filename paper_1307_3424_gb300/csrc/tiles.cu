@@ -5,13 +5,19 @@
 // multiple of 16 bytes:
 //   header   int32 row, int32 count, int32 segment id (row-major), int32 0
 //   mask     32 words, bit l of word r = cell (r, l) of the tile is stored
+//   prefix   32 uint16, entries stored in the tile rows before row r
 //   values   count values in row-major cell order, zero-padded to 16 bytes
 // so the records of one tile are one contiguous byte range.  A chunk is a run of
 // one tile's records holding about the same number of entries as the others;
 // a block of 4 warps takes one chunk.  Warp w handles tile rows 8w..8w+7 of
 // every record and lane l column l, so no two threads touch the same cell, the
 // gridding accumulators (and the degridding's cells of X) stay in registers,
-// and each warp has its rows' value loads in flight together.  The next
+// and each warp has its rows' value loads in flight together.  In the
+// degridding a warp reads its 8 rows' mask words and prefixes with three
+// 16-byte loads (the same address in every lane), so finding a lane's value
+// takes no shuffles; the gridding shuffles the words and scans their popcounts
+// (measured faster for it: it stays at 64 registers and 8 blocks per SM).  The
+// next
 // record's header and mask are loaded while the current one streams; its
 // offset follows from the current count.  The gridding also asks the TMA engine
 // to pull the chunk into L2 ahead of the warps (cp.async.bulk.prefetch.L2, 32 KB
@@ -101,13 +107,23 @@ k_stream(const int32_t *__restrict__ chunk_tile, const int64_t *__restrict__ chu
   float2 acc[kRows];
 #pragma unroll
   for (int rr = 0; rr < kRows; ++rr) acc[rr] = make_float2(0.f, 0.f);
+  static_assert(kRows == 8, "a warp reads 8 mask words and 8 prefixes");
+  // degridding: this warp's rows' mask words (two uint4) and prefixes (one uint4 of 8 uint16)
+  auto load_masks = [&](int64_t o, uint4 &a, uint4 &b, uint4 &p) {
+    const uint4 *mk = reinterpret_cast<const uint4 *>(stream + o + kRecHeader) + 2 * w;
+    a = __ldg(mk);
+    b = __ldg(mk + 1);
+    p = __ldg(reinterpret_cast<const uint4 *>(stream + o + kRecPrefix) + w);
+  };
   int64_t off = b0;
   int4 hdr = make_int4(0, 0, 0, 0);
-  unsigned word = 0;
+  uint4 wa = make_uint4(0, 0, 0, 0), wb = wa, pp = wa;
+  unsigned word = 0;                                     // gridding: mask word `lane`
   float2 yk = make_float2(0.f, 0.f);
   if (j0 < j1) {
     hdr = __ldg(reinterpret_cast<const int4 *>(stream + off));
-    word = __ldg(reinterpret_cast<const unsigned *>(stream + off + kRecHeader) + lane);
+    if (DEGRID) load_masks(off, wa, wb, pp);
+    else word = __ldg(reinterpret_cast<const unsigned *>(stream + off + kRecHeader) + lane);
     if (!DEGRID) {
       yk = __ldg(y + hdr.x);
       if (row_scale) yk = cscale(yk, __ldg(row_scale + hdr.x));
@@ -117,21 +133,34 @@ k_stream(const int32_t *__restrict__ chunk_tile, const int64_t *__restrict__ chu
     const int64_t offn = off + kRecValues + ((hdr.y * VB + 15) & ~15);
     const bool more = j + 1 < j1;
     int4 hdrn = make_int4(0, 0, 0, 0);
+    uint4 wan = make_uint4(0, 0, 0, 0), wbn = wan, ppn = wan;
     unsigned wordn = 0;
     if (more) {
       hdrn = __ldg(reinterpret_cast<const int4 *>(stream + offn));
-      wordn = __ldg(reinterpret_cast<const unsigned *>(stream + offn + kRecHeader) + lane);
+      if (DEGRID) load_masks(offn, wan, wbn, ppn);
+      else wordn = __ldg(reinterpret_cast<const unsigned *>(stream + offn + kRecHeader) + lane);
     }
     if (pf_thread) prefetch_to(off + kPfAhead);
-    const int pre = warp_excl_scan(__popc(word), lane);
     const unsigned char *vb = stream + off + kRecValues;
     float2 v[kRows];
+    if constexpr (DEGRID) {
+      const unsigned wrs[kRows] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+      const unsigned pps[kRows / 2] = {pp.x, pp.y, pp.z, pp.w};
 #pragma unroll
-    for (int rr = 0; rr < kRows; ++rr) {
-      const int r = kRows * w + rr;
-      const unsigned wr = __shfl_sync(0xffffffffu, word, r);
-      const int pr = __shfl_sync(0xffffffffu, pre, r);
-      v[rr] = ((wr >> lane) & 1u) ? gval<VDT>(vb + (pr + __popc(wr & lt)) * VB) : make_float2(0.f, 0.f);
+      for (int rr = 0; rr < kRows; ++rr) {
+        const unsigned wr = wrs[rr];
+        const int pr = int((pps[rr >> 1] >> (16 * (rr & 1))) & 0xffffu);
+        v[rr] = ((wr >> lane) & 1u) ? gval<VDT>(vb + (pr + __popc(wr & lt)) * VB) : make_float2(0.f, 0.f);
+      }
+    } else {
+      const int pre = warp_excl_scan(__popc(word), lane);
+#pragma unroll
+      for (int rr = 0; rr < kRows; ++rr) {
+        const int r = kRows * w + rr;
+        const unsigned wr = __shfl_sync(0xffffffffu, word, r);
+        const int pr = __shfl_sync(0xffffffffu, pre, r);
+        v[rr] = ((wr >> lane) & 1u) ? gval<VDT>(vb + (pr + __popc(wr & lt)) * VB) : make_float2(0.f, 0.f);
+      }
     }
     if constexpr (DEGRID) {
       float ax = 0.f, ay = 0.f;
@@ -141,12 +170,13 @@ k_stream(const int32_t *__restrict__ chunk_tile, const int64_t *__restrict__ chu
         ax = fmaf(v[rr].x, x.x, ax); ax = fmaf(-v[rr].y, x.y, ax);
         ay = fmaf(v[rr].x, x.y, ay); ay = fmaf(v[rr].y, x.x, ay);
       }
+      // warp sum of (ax, ay) in 5 shuffles: after one exchange even lanes carry
+      // pair sums of ax and odd lanes of ay, then both halve together
+      const bool odd = lane & 1;
+      float part = (odd ? ay : ax) + __shfl_xor_sync(0xffffffffu, odd ? ax : ay, 1);
 #pragma unroll
-      for (int o = 16; o; o >>= 1) {
-        ax += __shfl_xor_sync(0xffffffffu, ax, o);
-        ay += __shfl_xor_sync(0xffffffffu, ay, o);
-      }
-      if (lane == 0) out[int64_t(hdr.z) * kWarps + w] = make_float2(ax, ay);
+      for (int o = 2; o < 32; o <<= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+      if (lane < 2) reinterpret_cast<float *>(out + int64_t(hdr.z) * kWarps + w)[lane] = part;
     } else {
 #pragma unroll
       for (int rr = 0; rr < kRows; ++rr) {
@@ -161,6 +191,9 @@ k_stream(const int32_t *__restrict__ chunk_tile, const int64_t *__restrict__ chu
     }
     off = offn;
     hdr = hdrn;
+    wa = wan;
+    wb = wbn;
+    pp = ppn;
     word = wordn;
   }
   if constexpr (!DEGRID) {

@@ -24,8 +24,6 @@ namespace wproj {
 
 constexpr int kMaxTaps = 2 * WPROJ_DAUB_MAX_P;
 constexpr int kWT = 32;                       // analysis output tile (per sub-band); synthesis input tile
-constexpr int kWIn = 2 * kWT + kMaxTaps - 2;  // staged input side of an analysis tile
-constexpr int kWSyn = kWT + kMaxTaps / 2 - 1; // staged sub-band side of a synthesis tile
 constexpr int kWThreads = 256;
 constexpr int kWWarps = kWThreads / 32;
 
