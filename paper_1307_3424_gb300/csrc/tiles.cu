@@ -12,12 +12,10 @@
 // a block of 4 warps takes one chunk.  Warp w handles tile rows 8w..8w+7 of
 // every record and lane l column l, so no two threads touch the same cell, the
 // gridding accumulators (and the degridding's cells of X) stay in registers,
-// and each warp has its rows' value loads in flight together.  In the
-// degridding a warp reads its 8 rows' mask words and prefixes with three
-// 16-byte loads (the same address in every lane), so finding a lane's value
-// takes no shuffles; the gridding shuffles the words and scans their popcounts
-// (measured faster for it: it stays at 64 registers and 8 blocks per SM).  The
-// next
+// and each warp has its rows' value loads in flight together.  A warp reads
+// its 8 rows' mask words and prefixes with three 16-byte loads (the same
+// address in every lane), so finding a lane's value takes no shuffles or scans.
+// The next
 // record's header and mask are loaded while the current one streams; its
 // offset follows from the current count.  The gridding also asks the TMA engine
 // to pull the chunk into L2 ahead of the warps (cp.async.bulk.prefetch.L2, 32 KB
@@ -40,7 +38,8 @@ namespace {
 constexpr int kWarps = kStreamWarps;   // warps per block
 constexpr int kRows = 32 / kWarps;
 constexpr int kThreads = kWarps * 32;
-constexpr int kMinBlocks = 8;          // blocks per SM the register budget allows
+constexpr int kMinBlocks = 8;          // degridding: blocks per SM the register budget allows
+constexpr int kMinBlocksGrid = 7;      // gridding: its 8 accumulators need 72 registers
 constexpr int kPfAhead = 32768;        // gridding: bytes requested into L2 ahead of warp 0
 constexpr int kPfStep = 16384;
 
@@ -72,7 +71,7 @@ __device__ __forceinline__ int warp_excl_scan(int v, int lane) {
 }
 
 template <int VDT, bool DEGRID>
-__global__ void __launch_bounds__(kThreads, kMinBlocks)
+__global__ void __launch_bounds__(kThreads, DEGRID ? kMinBlocks : kMinBlocksGrid)
 k_stream(const int32_t *__restrict__ chunk_tile, const int64_t *__restrict__ chunk_lo,
          const int64_t *__restrict__ chunk_hi, const int64_t *__restrict__ rec_off, int stride,
          const unsigned char *__restrict__ stream, const float *__restrict__ row_scale,
@@ -108,7 +107,7 @@ k_stream(const int32_t *__restrict__ chunk_tile, const int64_t *__restrict__ chu
 #pragma unroll
   for (int rr = 0; rr < kRows; ++rr) acc[rr] = make_float2(0.f, 0.f);
   static_assert(kRows == 8, "a warp reads 8 mask words and 8 prefixes");
-  // degridding: this warp's rows' mask words (two uint4) and prefixes (one uint4 of 8 uint16)
+  // this warp's rows' mask words (two uint4) and prefixes (one uint4 of 8 uint16)
   auto load_masks = [&](int64_t o, uint4 &a, uint4 &b, uint4 &p) {
     const uint4 *mk = reinterpret_cast<const uint4 *>(stream + o + kRecHeader) + 2 * w;
     a = __ldg(mk);
@@ -118,12 +117,10 @@ k_stream(const int32_t *__restrict__ chunk_tile, const int64_t *__restrict__ chu
   int64_t off = b0;
   int4 hdr = make_int4(0, 0, 0, 0);
   uint4 wa = make_uint4(0, 0, 0, 0), wb = wa, pp = wa;
-  unsigned word = 0;                                     // gridding: mask word `lane`
   float2 yk = make_float2(0.f, 0.f);
   if (j0 < j1) {
     hdr = __ldg(reinterpret_cast<const int4 *>(stream + off));
-    if (DEGRID) load_masks(off, wa, wb, pp);
-    else word = __ldg(reinterpret_cast<const unsigned *>(stream + off + kRecHeader) + lane);
+    load_masks(off, wa, wb, pp);
     if (!DEGRID) {
       yk = __ldg(y + hdr.x);
       if (row_scale) yk = cscale(yk, __ldg(row_scale + hdr.x));
@@ -134,33 +131,20 @@ k_stream(const int32_t *__restrict__ chunk_tile, const int64_t *__restrict__ chu
     const bool more = j + 1 < j1;
     int4 hdrn = make_int4(0, 0, 0, 0);
     uint4 wan = make_uint4(0, 0, 0, 0), wbn = wan, ppn = wan;
-    unsigned wordn = 0;
     if (more) {
       hdrn = __ldg(reinterpret_cast<const int4 *>(stream + offn));
-      if (DEGRID) load_masks(offn, wan, wbn, ppn);
-      else wordn = __ldg(reinterpret_cast<const unsigned *>(stream + offn + kRecHeader) + lane);
+      load_masks(offn, wan, wbn, ppn);
     }
     if (pf_thread) prefetch_to(off + kPfAhead);
     const unsigned char *vb = stream + off + kRecValues;
     float2 v[kRows];
-    if constexpr (DEGRID) {
-      const unsigned wrs[kRows] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
-      const unsigned pps[kRows / 2] = {pp.x, pp.y, pp.z, pp.w};
+    const unsigned wrs[kRows] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+    const unsigned pps[kRows / 2] = {pp.x, pp.y, pp.z, pp.w};
 #pragma unroll
-      for (int rr = 0; rr < kRows; ++rr) {
-        const unsigned wr = wrs[rr];
-        const int pr = int((pps[rr >> 1] >> (16 * (rr & 1))) & 0xffffu);
-        v[rr] = ((wr >> lane) & 1u) ? gval<VDT>(vb + (pr + __popc(wr & lt)) * VB) : make_float2(0.f, 0.f);
-      }
-    } else {
-      const int pre = warp_excl_scan(__popc(word), lane);
-#pragma unroll
-      for (int rr = 0; rr < kRows; ++rr) {
-        const int r = kRows * w + rr;
-        const unsigned wr = __shfl_sync(0xffffffffu, word, r);
-        const int pr = __shfl_sync(0xffffffffu, pre, r);
-        v[rr] = ((wr >> lane) & 1u) ? gval<VDT>(vb + (pr + __popc(wr & lt)) * VB) : make_float2(0.f, 0.f);
-      }
+    for (int rr = 0; rr < kRows; ++rr) {
+      const unsigned wr = wrs[rr];
+      const int pr = int((pps[rr >> 1] >> (16 * (rr & 1))) & 0xffffu);
+      v[rr] = ((wr >> lane) & 1u) ? gval<VDT>(vb + (pr + __popc(wr & lt)) * VB) : make_float2(0.f, 0.f);
     }
     if constexpr (DEGRID) {
       float ax = 0.f, ay = 0.f;
@@ -194,7 +178,6 @@ k_stream(const int32_t *__restrict__ chunk_tile, const int64_t *__restrict__ chu
     wa = wan;
     wb = wbn;
     pp = ppn;
-    word = wordn;
   }
   if constexpr (!DEGRID) {
     float2 *o = out + int64_t(c) * 1024;
