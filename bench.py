@@ -88,6 +88,24 @@ def dist_env():
     return ws, rank, local
 
 
+def reduce_times_max(times_ms, ws, device=None):
+    """Job time of weak-scaled replicas: the maximum over ranks of each timed
+    region (a no-op for one process).  Collective over the default process
+    group (NCCL on GPUs, gloo in the CPU tests)."""
+    if ws <= 1:
+        return [float(t) for t in times_ms]
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([float(t) for t in times_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return [float(v) for v in tt.cpu()]
+
+
+def job_rate(units_per_rank, ws, t_ms):
+    """Whole-job throughput: every rank processed units_per_rank in the job time."""
+    return units_per_rank * ws / (t_ms * 1e-3)
+
+
 def workload_config(wl, e, extra=None):
     cfg = {"workload": f"{wl.name}_e{e}", "N": wl.N, "G": 2 * wl.N, "M": wl.M, "e": e,
            "uv": f"{wl.uv} sigma={wl.sigma_uv}B", "wd_max": wl.wd_max, "kb_support": wl.W,
@@ -341,11 +359,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     t_e2e_ms = e0.elapsed_time(e1)
 
-    if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_ms, t_e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms, t_e2e_ms = float(tt[0]), float(tt[1])
+    t_ms, t_e2e_ms = reduce_times_max([t_ms, t_e2e_ms], ws, dev)
 
     # ---- roofline of the dominant kernel (degridding or gridding)
     peaks = {}
@@ -378,8 +392,8 @@ def run_ours(args):
             "degrid_frac": alg_deg / (deg_ms * 1e-3) / 1e9 / hbm_peak,
             "grid_frac": alg_grid / (grid_ms * 1e-3) / 1e9 / hbm_peak}
 
-    value = PAIRS_PER_STEP * args.steps * ws / (t_ms * 1e-3)
-    e2e_value = PAIRS_PER_STEP * args.steps * ws / (t_e2e_ms * 1e-3)
+    value = job_rate(PAIRS_PER_STEP * args.steps, ws, t_ms)
+    e2e_value = job_rate(PAIRS_PER_STEP * args.steps, ws, t_e2e_ms)
     out = None
     if rank == 0:
         cpu = None

@@ -168,3 +168,35 @@ def test_reconstruction_with_screens(wp):
     print(f"screens: SNR oracle {s_o:.3f} dB, GPU {s_g:.3f} dB")
     assert abs(s_o - s_g) <= 0.1
     plan.close()
+
+
+@pytest.mark.parametrize("fmt", ["columns", "mask"])
+def test_screened_rows_at_size_sampled(wp, fmt):
+    # N = 128 (64 grid tiles), M = 4096, 8 screens: sampled rows against the oracle
+    # (values, kept energy, cardinality) and the adjoint identity of the whole operator
+    N, M, e = 128, 4096, 0.99
+    uvw, screens, sid = problem(N, M, 8, 31)
+    geo = O.Geometry(N, L)
+    plan = gpu_plan(wp, N, uvw, screens, sid, e, fmt)
+    c = plan.csr()
+    G = geo.G
+    num = den = 0.0
+    for k in np.random.default_rng(5).choice(M, 12, replace=False):
+        col, val = (t.cpu().numpy() for t in c.rows(int(k), int(k) + 1))
+        val = val.astype(np.complex128)
+        K, j0u, j0v = O.kernel_box(geo, *uvw[k], G, screens[sid[k]].astype(np.complex128))
+        su = ((col // G - j0u + G // 2) % G) - G // 2
+        sv = ((col % G - j0v + G // 2) % G) - G // 2
+        vo = K[su % G, sv % G]
+        num += np.sum(np.abs(val - vo) ** 2)
+        den += np.sum(np.abs(vo) ** 2)
+        assert math.fsum(np.abs(vo) ** 2) >= e * math.fsum(np.abs(K.ravel()) ** 2)
+        assert col.size <= O.select_sort(K, O.box_columns(geo, j0u, j0v, G), e + 2e-5).size
+    assert math.sqrt(num / den) <= 1e-5
+    rng = np.random.default_rng(6)
+    x = torch.from_numpy(rng.standard_normal((N, N)).astype(np.float32)).to(dev())
+    yv = torch.from_numpy((rng.standard_normal(M) + 1j * rng.standard_normal(M)).astype(np.complex64)).to(dev())
+    lhs = torch.vdot(yv.to(torch.complex128), plan.phi(x).to(torch.complex128)).real.item()
+    rhs = float((x.double() * plan.phi_adj(yv).double()).sum().item())
+    assert abs(lhs - rhs) <= 1e-4 * abs(lhs)
+    plan.close()

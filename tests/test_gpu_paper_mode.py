@@ -160,3 +160,39 @@ def test_reconstruction_in_paper_mode(wp):
     assert min(snr_o) - 0.1 <= s_g <= max(snr_o) + 0.1, (s_g, snr_o)
     assert info.final_resid <= eps * 1.05
     plan.close()
+
+
+def test_paper_mode_at_256_sampled(wp):
+    # N = 256 (G = 512, 256 tiles), 20 % coverage, E = 0.75: sampled rows against
+    # the oracle's support rule and values; Phi' against the literal definition
+    # on sampled visibilities at E = 1
+    N, E = 256, 0.75
+    prob = synth.paper_problem(N, 0.2, seed=4)
+    geo = O.paper_geometry(N, L)
+    M = prob.uvw.shape[0]
+    ug = torch.from_numpy(prob.uvw).to(dev())
+    plan = paper_plan(wp, N)
+    plan.build_kernels(ug, E)
+    c = plan.csr()
+    G = 2 * N
+    num = den = 0.0
+    for k in np.random.default_rng(8).choice(M, 10, replace=False):
+        col, val = (t.cpu().numpy() for t in c.rows(int(k), int(k) + 1))
+        val = val.astype(np.complex128)
+        K, j0u, j0v = O.kernel_box(geo, *prob.uvw[k], G)
+        su = ((col // G - j0u + G // 2) % G) - G // 2
+        sv = ((col % G - j0v + G // 2) % G) - G // 2
+        vo = K[su % G, sv % G]
+        num += np.sum(np.abs(val - vo) ** 2)
+        den += np.sum(np.abs(vo) ** 2)
+        assert math.fsum(np.abs(vo) ** 2) >= E
+        assert col.size <= O.select_sort(K, O.box_columns(geo, j0u, j0v, G), E + 2e-5).size
+    assert math.sqrt(num / den) <= 1e-5
+    # E = 1 keeps whole G x G rows: build the sampled visibilities alone
+    pick = np.random.default_rng(10).choice(M, 16, replace=False)
+    plan.build_kernels(torch.from_numpy(np.ascontiguousarray(prob.uvw[pick])).to(dev()), 1.0)
+    x = np.random.default_rng(9).standard_normal((N, N))
+    y = plan.phi(torch.from_numpy(x.astype(np.float32)).to(dev())).cpu().numpy()
+    yd = O.paper_visibilities_direct(N, L, x, prob.uvw[pick])
+    assert rel(y, yd) <= 1e-5
+    plan.close()
