@@ -18,7 +18,7 @@
 // The next
 // record's header and mask are loaded while the current one streams; its
 // offset follows from the current count.  The gridding also asks the TMA engine
-// to pull the chunk into L2 ahead of the warps (cp.async.bulk.prefetch.L2, 32 KB
+// to pull the chunk into L2 ahead of the warps (cp.async.bulk.prefetch.L2, 16 KB
 // ahead); in the degridding that measured slower and is off.  Blocks take
 // chunks in a strided order (chunk = block * stride mod chunks), which spreads
 // the concurrently read chunks over more tiles (measured faster than in order).
@@ -40,8 +40,8 @@ constexpr int kRows = 32 / kWarps;
 constexpr int kThreads = kWarps * 32;
 constexpr int kMinBlocks = 8;          // degridding: blocks per SM the register budget allows
 constexpr int kMinBlocksGrid = 7;      // gridding: its 8 accumulators need 72 registers
-constexpr int kPfAhead = 32768;        // gridding: bytes requested into L2 ahead of warp 0
-constexpr int kPfStep = 16384;
+constexpr int kPfAhead = 16384;        // gridding: bytes requested into L2 ahead of warp 0
+constexpr int kPfStep = 8192;
 
 __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
