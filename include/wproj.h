@@ -444,8 +444,10 @@ wproj_status wproj_batch_phi_adj(wproj_batch *b, const void *y, float *x_re, voi
  * (host) per problem and one parameter set; ||Phi_p||^2 is always estimated per
  * problem by prm->power_iters power iterations (prm->phi_norm2 is ignored).
  * prm->resume continues the batch's state.  The iterations replay a captured
- * CUDA graph (recaptured when y, inner_iters or lambda change).  x_out: all
- * images, concatenated. */
+ * CUDA graph (recaptured when y, inner_iters, lambda or the basis change).
+ * x_out: all images, concatenated.  prm->psi selects the sparsity basis as for
+ * wproj_solve_bpdn (0 Dirac, p Daubechies-p over prm->psi_levels levels; every
+ * side must be divisible by 2^levels, else WPROJ_ERR_INVALID_ARG). */
 wproj_status wproj_batch_solve_bpdn(wproj_batch *b, const void *y, const double *eps, const wproj_dr_params *prm,
                                     float *x_out, void *stream);
 wproj_status wproj_batch_get_info(const wproj_batch *b, wproj_batch_info *out);

@@ -48,6 +48,9 @@ struct wproj_batch {
   wproj::DevBuf piece_partial, grid_partial;
   // work buffers and Douglas-Rachford state
   wproj::DevBuf Xt, Xt2, interb, x, z, u, r, xtmp, scal, part, eps, mu;
+  wproj::DevBuf zi, alpha, wwork;   // wavelet Psi: Psi z, Psi^T x, transform scratch
+  int max_n = 0;                    // largest image side
+  int pow2_div = 0;                 // largest power of two dividing every side
   bool dr_valid = false;
   // one DR iteration captured as a graph
   cudaStream_t cap = nullptr;
@@ -55,6 +58,7 @@ struct wproj_batch {
   const void *graph_y = nullptr;
   int graph_inner = -1;
   double graph_lambda = 0;
+  int graph_psi = -1, graph_levels = -1;
   int64_t iter_launches = 0;   // kernels in the captured iteration
   int64_t launches = 0;        // kernels launched by operator and solver calls
   ~wproj_batch() {
@@ -321,9 +325,14 @@ wproj_status ensure_solver(wproj_batch *b) {
 }
 
 // One Douglas-Rachford iteration of every problem (launches only: graph-capturable).
-wproj_status dr_iteration(wproj_batch *b, const float2 *y, int inner, float lambda, cudaStream_t s) {
+// psi > 0: z holds Daubechies-psi coefficients; the projection runs on zi = Psi z
+// and its result is analysed again before the update (exact: Psi is orthonormal).
+wproj_status dr_iteration(wproj_batch *b, const float2 *y, int inner, float lambda, int psi, int levels,
+                          cudaStream_t s) {
   const BProb *tab = b->tab.as<BProb>();
-  float *z = b->z.as<float>(), *x = b->x.as<float>();
+  float *zc = b->z.as<float>(), *x = b->x.as<float>();
+  float *z = psi ? b->zi.as<float>() : zc;   // the image the projection starts from
+  if (psi) WPROJ_TRY(batch_idwt2(tab, b->np, b->max_n, levels, psi, zc, z, b->wwork.as<float>(), &b->launches, s));
   float2 *u = b->u.as<float2>(), *r = b->r.as<float2>();
   double *scal = b->scal.as<double>(), *part = b->part.as<double>();
   const int nbm = nbx_for(b->max_m), nbn = nbx_for(b->max_img);
@@ -338,7 +347,12 @@ wproj_status dr_iteration(wproj_batch *b, const float2 *y, int inner, float lamb
     b->launches += 3;
   }
   WPROJ_TRY(bphi_adj(b, u, x, z, 1, s));     // x = P_B(z)
-  k_bs_dr_update<<<dim3(nbn, b->np), kBT, 0, s>>>(tab, x, z, lambda, scal);
+  float *px = x;
+  if (psi) {
+    px = b->alpha.as<float>();
+    WPROJ_TRY(batch_dwt2(tab, b->np, b->max_n, levels, psi, x, px, b->wwork.as<float>(), &b->launches, s));
+  }
+  k_bs_dr_update<<<dim3(nbn, b->np), kBT, 0, s>>>(tab, px, zc, lambda, scal);
   WPROJ_CHECK_LAUNCH("batch dr update");
   b->launches += 1;
   return WPROJ_OK;
@@ -417,6 +431,8 @@ wproj_status batch_build_impl(wproj_batch *b, const double *uvw, const int64_t *
   int64_t img = 0, grid = 0, inter = 0, inva = 0, nnz = 0, nseg = 0, tiles = 0;
   vis = 0;
   b->max_m = b->max_img = 0;
+  b->max_n = 0;
+  b->pow2_div = 1 << 30;
   for (int p = 0; p < np; ++p) {
     const wproj_plan *pl = plans[p];
     BProb &P = b->prob[p];
@@ -441,6 +457,8 @@ wproj_status batch_build_impl(wproj_batch *b, const double *uvw, const int64_t *
     tiles += int64_t(P.nT) * P.nT;
     b->max_m = std::max(b->max_m, P.m);
     b->max_img = std::max<int64_t>(b->max_img, int64_t(P.N) * P.N);
+    b->max_n = std::max(b->max_n, P.N);
+    b->pow2_div = std::min(b->pow2_div, P.N & -P.N);
   }
   if (grid >= (int64_t(1) << 31)) return fail(WPROJ_ERR_UNSUPPORTED, "batch: grids exceed 2^31 cells in total");
   b->m = vis;
@@ -596,10 +614,22 @@ wproj_status batch_solve_impl(wproj_batch *b, const float2 *y, const double *eps
   WPROJ_CUDA(cudaMemcpyAsync(b->eps.ptr, eps, sizeof(double) * b->np, cudaMemcpyHostToDevice, s));
   const BProb *tab = b->tab.as<BProb>();
   const int nbn = nbx_for(b->max_img);
+  const int psi = prm.psi, lev = prm.psi_levels;
+  if (psi) {
+    WPROJ_TRY(b->zi.ensure(sizeof(float) * b->img));
+    WPROJ_TRY(b->alpha.ensure(sizeof(float) * b->img));
+    WPROJ_TRY(b->wwork.ensure(sizeof(float) * (b->img / 2 + 1)));
+  }
   if (!resume) {
     WPROJ_TRY(power_mu(b, prm.power_iters, s));
-    // z0 = Re Phi^H y, gamma = frac max|z0|, u = 0
-    WPROJ_TRY(bphi_adj(b, y, b->z.as<float>(), nullptr, 0, s));
+    // z0 = Psi^T Re Phi^H y, gamma = frac max|z0|, u = 0
+    if (psi) {
+      WPROJ_TRY(bphi_adj(b, y, b->x.as<float>(), nullptr, 0, s));
+      WPROJ_TRY(batch_dwt2(tab, b->np, b->max_n, lev, psi, b->x.as<float>(), b->z.as<float>(),
+                           b->wwork.as<float>(), &b->launches, s));
+    } else {
+      WPROJ_TRY(bphi_adj(b, y, b->z.as<float>(), nullptr, 0, s));
+    }
     k_bs_image_part<0><<<dim3(nbn, b->np), kBT, 0, s>>>(tab, b->z.as<float>(), b->part.as<double>());
     k_bs_image_scalar<0><<<ceil_div(b->np, 128), 128, 0, s>>>(b->np, nbn, b->part.as<double>(), prm.gamma_frac,
                                                               b->scal.as<double>());
@@ -608,14 +638,15 @@ wproj_status batch_solve_impl(wproj_batch *b, const float2 *y, const double *eps
   }
   b->dr_valid = true;
   if (prm.iters > 0) {
-    if (!b->dr_exec || b->graph_y != y || b->graph_inner != prm.inner_iters || b->graph_lambda != prm.lambda) {
+    if (!b->dr_exec || b->graph_y != y || b->graph_inner != prm.inner_iters || b->graph_lambda != prm.lambda ||
+        b->graph_psi != psi || b->graph_levels != lev) {
       if (b->dr_exec) cudaGraphExecDestroy(b->dr_exec);
       b->dr_exec = nullptr;
       if (!b->cap) WPROJ_CUDA(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
       cudaGraph_t g = nullptr;
       WPROJ_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
       const int64_t l0 = b->launches;
-      wproj_status st = dr_iteration(b, y, prm.inner_iters, float(prm.lambda), b->cap);
+      wproj_status st = dr_iteration(b, y, prm.inner_iters, float(prm.lambda), psi, lev, b->cap);
       const cudaError_t ce = cudaStreamEndCapture(b->cap, &g);
       if (st != WPROJ_OK) {
         if (g) cudaGraphDestroy(g);
@@ -628,6 +659,8 @@ wproj_status batch_solve_impl(wproj_batch *b, const float2 *y, const double *eps
       b->graph_y = y;
       b->graph_inner = prm.inner_iters;
       b->graph_lambda = prm.lambda;
+      b->graph_psi = psi;
+      b->graph_levels = lev;
       b->iter_launches = b->launches - l0;   // kernels per replay
       b->launches = l0;
     }
@@ -635,6 +668,11 @@ wproj_status batch_solve_impl(wproj_batch *b, const float2 *y, const double *eps
     b->launches += b->iter_launches * prm.iters;
   }
   float *src = prm.iters > 0 ? b->x.as<float>() : b->z.as<float>();
+  if (prm.iters == 0 && psi) {   // x = Psi z0
+    WPROJ_TRY(batch_idwt2(tab, b->np, b->max_n, lev, psi, b->z.as<float>(), b->x.as<float>(), b->wwork.as<float>(),
+                          &b->launches, s));
+    src = b->x.as<float>();
+  }
   WPROJ_CUDA(cudaMemcpyAsync(x_out, src, sizeof(float) * b->img, cudaMemcpyDeviceToDevice, s));
   return WPROJ_OK;
 }
@@ -722,7 +760,9 @@ wproj_status wproj_batch_solve_bpdn(wproj_batch *b, const void *y, const double 
   if (q.iters < 0 || q.inner_iters < 1 || q.power_iters < 1 || !(q.lambda > 0.0 && q.lambda < 2.0) ||
       !(q.gamma_frac >= 0.0))
     return fail(WPROJ_ERR_INVALID_ARG, "batch_solve_bpdn: invalid parameters");
-  if (q.psi != 0) return fail(WPROJ_ERR_UNSUPPORTED, "batch_solve_bpdn: the batched solver uses the Dirac basis");
+  if (q.psi < 0 || q.psi > WPROJ_DAUB_MAX_P) return fail(WPROJ_ERR_INVALID_ARG, "batch_solve_bpdn: psi");
+  if (q.psi && (q.psi_levels < 1 || q.psi_levels > 29 || b->pow2_div % (1 << q.psi_levels) != 0))
+    return fail(WPROJ_ERR_INVALID_ARG, "batch_solve_bpdn: every N must be divisible by 2^psi_levels");
   for (int p = 0; p < b->np; ++p)
     if (!(eps[p] >= 0.0) || !isfinite(eps[p]))
       return fail(WPROJ_ERR_INVALID_ARG, "batch_solve_bpdn: eps must be finite and >= 0");

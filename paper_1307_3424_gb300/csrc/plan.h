@@ -217,6 +217,11 @@ wproj_status dwt2_impl(int N, int levels, int p, const float *x, float *alpha, f
                        cudaStream_t s);
 wproj_status idwt2_impl(int N, int levels, int p, const float *alpha, float *x, float *work, int64_t *launches,
                         cudaStream_t s);
+// every problem of a batch (tab[np] on the device, images at img_off); work: sum N^2/2 floats
+wproj_status batch_dwt2(const BProb *tab, int np, int maxN, int levels, int p, const float *x, float *alpha,
+                        float *work, int64_t *launches, cudaStream_t s);
+wproj_status batch_idwt2(const BProb *tab, int np, int maxN, int levels, int p, const float *alpha, float *x,
+                         float *work, int64_t *launches, cudaStream_t s);
 
 // ops.cu
 wproj_status degrid(wproj_plan *p, const float2 *Xt, float2 *y, cudaStream_t s);

@@ -169,9 +169,8 @@ __device__ __forceinline__ int wrap_up(int i, int n, bool big) {
 // the inputs of 8 consecutive outputs in registers (two shared-memory loads per
 // output instead of L), the tap count L = 2p a compile-time constant.
 template <int L>
-__global__ void __launch_bounds__(kWThreads)
-k_dwt_level(const float *__restrict__ src, int lds, int n, const Taps t, float *__restrict__ ll, int ldl,
-            float *__restrict__ coef, int ldc) {
+__device__ __forceinline__ void dwt_level_body(const float *__restrict__ src, int lds, int n, const Taps &t,
+                                               float *__restrict__ ll, int ldl, float *__restrict__ coef, int ldc) {
   constexpr int span = 2 * kWT + L - 2;
   constexpr int SEG = 8, NW = 2 * SEG + L - 2;      // outputs per task, inputs per task
   __shared__ float in[span][span + 1];
@@ -240,9 +239,8 @@ k_dwt_level(const float *__restrict__ src, int lds, int n, const Taps t, float *
 // 64 x 64 output tile from (32 + L/2 - 1)^2 samples of each band; each task keeps
 // the band samples of 16 consecutive outputs in registers.
 template <int L>
-__global__ void __launch_bounds__(kWThreads)
-k_idwt_level(const float *__restrict__ ll, int ldl, const float *__restrict__ coef, int ldc, int n, const Taps t,
-             float *__restrict__ dst, int ldd) {
+__device__ __forceinline__ void idwt_level_body(const float *__restrict__ ll, int ldl, const float *__restrict__ coef,
+                                                int ldc, int n, const Taps &t, float *__restrict__ dst, int ldd) {
   constexpr int off = L / 2 - 1;                   // staged index = band index - (j0/2 - off)
   constexpr int span = kWT + off;
   constexpr int SEG = 16, NW = SEG / 2 + off;      // outputs per task, band samples per task
@@ -312,6 +310,55 @@ k_idwt_level(const float *__restrict__ ll, int ldl, const float *__restrict__ co
       if (g1 < n && g2 < n) dst[int64_t(g1) * ldd + g2] = x;
     }
   }
+}
+
+template <int L>
+__global__ void __launch_bounds__(kWThreads)
+k_dwt_level(const float *__restrict__ src, int lds, int n, const Taps t, float *__restrict__ ll, int ldl,
+            float *__restrict__ coef, int ldc) {
+  dwt_level_body<L>(src, lds, n, t, ll, ldl, coef, ldc);
+}
+
+template <int L>
+__global__ void __launch_bounds__(kWThreads)
+k_idwt_level(const float *__restrict__ ll, int ldl, const float *__restrict__ coef, int ldc, int n, const Taps t,
+             float *__restrict__ dst, int ldd) {
+  idwt_level_body<L>(ll, ldl, coef, ldc, n, t, dst, ldd);
+}
+
+// Batches: level lv of every problem (blockIdx.z) at once.  Problem p's image
+// sits at img_off in x / alpha, its two ping-pong low-low bands (N^2 / 4 floats
+// each) at img_off / 2 in work; the grid is sized for the largest problem and
+// the other problems' surplus tiles return at once.
+template <int L>
+__global__ void __launch_bounds__(kWThreads)
+k_bdwt_level(const BProb *__restrict__ tab, int lv, int levels, const float *__restrict__ x,
+             float *__restrict__ alpha, float *__restrict__ work, const Taps t) {
+  const BProb P = tab[blockIdx.z];
+  const int N = P.N, n = N >> lv, h = n / 2;
+  if (int(blockIdx.x) * kWT >= h || int(blockIdx.y) * kWT >= h) return;
+  float *a = alpha + P.img_off;
+  float *ping0 = work + P.img_off / 2, *ping1 = ping0 + int64_t(N) * N / 4;
+  const float *src = lv == 0 ? x + P.img_off : (((lv - 1) & 1) ? ping1 : ping0);
+  const int lds = lv == 0 ? N : n;
+  const bool last = lv == levels - 1;
+  dwt_level_body<L>(src, lds, n, t, last ? a : ((lv & 1) ? ping1 : ping0), last ? N : h, a, N);
+}
+
+template <int L>
+__global__ void __launch_bounds__(kWThreads)
+k_bidwt_level(const BProb *__restrict__ tab, int lv, int levels, const float *__restrict__ alpha,
+              float *__restrict__ x, float *__restrict__ work, const Taps t) {
+  const BProb P = tab[blockIdx.z];
+  const int N = P.N, n = N >> lv;
+  if (int(blockIdx.x) * 2 * kWT >= n || int(blockIdx.y) * 2 * kWT >= n) return;
+  const float *a = alpha + P.img_off;
+  float *ping0 = work + P.img_off / 2, *ping1 = ping0 + int64_t(N) * N / 4;
+  const bool deepest = lv == levels - 1;
+  const float *ll = deepest ? a : (((lv + 1) & 1) ? ping1 : ping0);
+  const int ldl = deepest ? N : n / 2;
+  float *dst = lv == 0 ? x + P.img_off : ((lv & 1) ? ping1 : ping0);
+  idwt_level_body<L>(ll, ldl, a, N, n, t, dst, lv == 0 ? N : n);
 }
 
 wproj_status check_psi(int N, int levels, int p) {
@@ -384,6 +431,54 @@ wproj_status idwt2_impl(int N, int levels, int p, const float *alpha, float *x, 
     ll = dst;
     ldl = ldd;
     n *= 2;
+  }
+  if (launches) *launches += levels;
+  return WPROJ_OK;
+}
+
+// Batched transforms: every problem's image (tab[np] on the device, sides up to
+// maxN) through `levels` levels; work holds sum N^2 / 2 floats.
+wproj_status batch_dwt2(const BProb *tab, int np, int maxN, int levels, int p, const float *x, float *alpha,
+                        float *work, int64_t *launches, cudaStream_t s) {
+  WPROJ_TRY(check_psi(maxN, levels, p));
+  double hd[kMaxTaps];
+  WPROJ_TRY(daubechies_taps_impl(p, hd));
+  const Taps t = make_taps(hd, 2 * p);
+  for (int lv = 0; lv < levels; ++lv) {
+    const int h = (maxN >> lv) / 2;
+    const dim3 grid(ceil_div(h, kWT), ceil_div(h, kWT), np);
+    switch (t.len) {
+#define BDWT_CASE(L) \
+  case L: k_bdwt_level<L><<<grid, kWThreads, 0, s>>>(tab, lv, levels, x, alpha, work, t); break;
+      BDWT_CASE(2) BDWT_CASE(4) BDWT_CASE(6) BDWT_CASE(8) BDWT_CASE(10)
+      BDWT_CASE(12) BDWT_CASE(14) BDWT_CASE(16) BDWT_CASE(18) BDWT_CASE(20)
+#undef BDWT_CASE
+      default: return fail(WPROJ_ERR_INVALID_ARG, "Daubechies order out of range");
+    }
+    WPROJ_CHECK_LAUNCH("batch wavelet analysis level");
+  }
+  if (launches) *launches += levels;
+  return WPROJ_OK;
+}
+
+wproj_status batch_idwt2(const BProb *tab, int np, int maxN, int levels, int p, const float *alpha, float *x,
+                         float *work, int64_t *launches, cudaStream_t s) {
+  WPROJ_TRY(check_psi(maxN, levels, p));
+  double hd[kMaxTaps];
+  WPROJ_TRY(daubechies_taps_impl(p, hd));
+  const Taps t = make_taps(hd, 2 * p);
+  for (int lv = levels - 1; lv >= 0; --lv) {
+    const int n = maxN >> lv;
+    const dim3 grid(ceil_div(n, 2 * kWT), ceil_div(n, 2 * kWT), np);
+    switch (t.len) {
+#define BIDWT_CASE(L) \
+  case L: k_bidwt_level<L><<<grid, kWThreads, 0, s>>>(tab, lv, levels, alpha, x, work, t); break;
+      BIDWT_CASE(2) BIDWT_CASE(4) BIDWT_CASE(6) BIDWT_CASE(8) BIDWT_CASE(10)
+      BIDWT_CASE(12) BIDWT_CASE(14) BIDWT_CASE(16) BIDWT_CASE(18) BIDWT_CASE(20)
+#undef BIDWT_CASE
+      default: return fail(WPROJ_ERR_INVALID_ARG, "Daubechies order out of range");
+    }
+    WPROJ_CHECK_LAUNCH("batch wavelet synthesis level");
   }
   if (launches) *launches += levels;
   return WPROJ_OK;

@@ -564,13 +564,13 @@ class Batch:
 
     def solve_bpdn(self, y: torch.Tensor, eps, iters: int = 50, inner_iters: int = 10, gamma_frac: float = 1e-2,
                    lam: float = 1.0, power_iters: int = 100, x_out: torch.Tensor | None = None,
-                   resume: bool = False, stream=None) -> torch.Tensor:
+                   resume: bool = False, psi: int = 0, psi_levels: int = 4, stream=None) -> torch.Tensor:
         if y.dtype != torch.complex64 or y.numel() != self.m:
             raise WprojError(ERR_INVALID_ARG, f"y must hold {self.m} complex64 visibilities")
         eps = [float(v) for v in eps]
         if len(eps) != len(self.ns):
             raise WprojError(ERR_INVALID_ARG, "one eps per problem")
-        prm = DRParams(iters, inner_iters, gamma_frac, lam, 0.0, power_iters, 1 if resume else 0)
+        prm = DRParams(iters, inner_iters, gamma_frac, lam, 0.0, power_iters, 1 if resume else 0, psi, psi_levels)
         if x_out is None:
             x_out = torch.empty(self.pixels, dtype=torch.float32, device=y.device)
         arr = (ctypes.c_double * len(eps))(*eps)

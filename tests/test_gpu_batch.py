@@ -165,3 +165,37 @@ def test_batch_bad_input(wp):
     with pytest.raises(wp.WprojError):
         b.build_kernels(uvw, [2, 1], 1.5)                             # e outside (0, 1]
     b.close()
+
+
+def test_batch_db8_solver_matches_single_plans(wp):
+    # Eq. 7 with the Daubechies-8 basis in the batched solver: problems of
+    # different sides, levels 3 (every side divisible by 8), against single plans
+    ns, ms = [32, 64, 16, 64, 128], [400, 1500, 100, 900, 3000]
+    uvws, _ = make_case(ns, ms, seed=17)
+    rng = np.random.default_rng(18)
+    skies = [synth.blob_sky(rng, n, 5) for n in ns]
+    b = build_batch(wp, ns, uvws, 0.99)
+    x_cat = torch.from_numpy(np.concatenate([x.ravel() for x in skies]).astype(np.float32)).to(dev())
+    sig = [synth.noise_sigma(x, 30.0) for x in skies]
+    noise = np.concatenate([synth.complex_noise(rng, m, s) for m, s in zip(ms, sig)]).astype(np.complex64)
+    y = b.phi(x_cat) + torch.from_numpy(noise).to(dev())
+    eps = [O.epsilon_chi2(s, m) for s, m in zip(sig, ms)]
+    xb = b.solve_bpdn(y, eps, iters=12, power_iters=50, psi=8, psi_levels=3)
+    xd = b.solve_bpdn(y, eps, iters=12, power_iters=50)            # the Dirac graph is recaptured
+    assert not torch.equal(xb, xd)
+    x0 = b.solve_bpdn(y, eps, iters=0, psi=8, psi_levels=3)        # Psi z0 = Re Phi^H y
+    assert rel(x0.cpu().numpy(), b.phi_adj(y).cpu().numpy()) <= 2e-6
+    ys = b.split_vis(y)
+    for i, (n, uvw) in enumerate(zip(ns, uvws)):
+        p = wp.Plan(n, L, box="rule", index_format="columns")
+        p.build_kernels(torch.from_numpy(uvw).to(dev()), 0.99)
+        x1, _ = p.solve_bpdn(ys[i].contiguous(), eps[i], iters=12, power_iters=50, psi=8, psi_levels=3)
+        xbi = b.split_images(xb)[i].cpu().numpy()
+        s_b = O.snr_db(skies[i], xbi.astype(np.float64))
+        s_1 = O.snr_db(skies[i], x1.cpu().numpy().astype(np.float64))
+        assert abs(s_b - s_1) <= 0.1, (i, s_b, s_1)
+        assert rel(xbi, x1.cpu().numpy()) <= 1e-3
+        p.close()
+    with pytest.raises(wp.WprojError):
+        b.solve_bpdn(y, eps, iters=1, psi=8, psi_levels=5)            # 16 is not divisible by 32
+    b.close()
