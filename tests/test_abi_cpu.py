@@ -59,3 +59,21 @@ def test_invalid_plan_arguments_rejected_on_host(built_lib):
               wproj.GridDesc(64, 4, 0.9, 0, 0, 0, 0)):     # 1 - 2L^2 < 0
         assert L.wproj_plan_create(ctypes.byref(h), ctypes.byref(d)) == wproj.ERR_INVALID_ARG
         assert L.wproj_last_error()
+
+
+def test_daubechies_taps_on_the_host_match_oracle(built_lib):
+    # the library's tap generator runs on the host (spectral factorisation in
+    # double): its taps against the oracle's for every supported order
+    import numpy as np
+    from oracle import wavelet_oracle as W
+    for p in range(1, 11):
+        h = np.array(wproj.daubechies_taps(p))
+        assert np.allclose(h, W.daubechies_taps(p), rtol=0, atol=1e-12), p
+    for p in (0, 11):
+        with pytest.raises(wproj.WprojError):
+            wproj.daubechies_taps(p)
+
+
+def test_dr_defaults_select_the_dirac_basis(built_lib):
+    p = wproj.dr_defaults()
+    assert p.psi == 0 and p.psi_levels == 4
