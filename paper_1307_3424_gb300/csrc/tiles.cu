@@ -81,7 +81,7 @@ k_stream(const int32_t *__restrict__ chunk_tile, const int64_t *__restrict__ chu
   constexpr bool kPrefetch = !DEGRID;
   const int c = int((unsigned long long)blockIdx.x * unsigned(stride) % gridDim.x);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const unsigned lt = (1u << lane) - 1u;
+  const unsigned lbit = 1u << lane, lt = lbit - 1u;
   const int64_t j0 = chunk_lo[c], j1 = chunk_hi[c];
   const int64_t b0 = rec_off[j0], b1 = rec_off[j1];
   int64_t pf = b0;
@@ -144,7 +144,7 @@ k_stream(const int32_t *__restrict__ chunk_tile, const int64_t *__restrict__ chu
     for (int rr = 0; rr < kRows; ++rr) {
       const unsigned wr = wrs[rr];
       const int pr = int((pps[rr >> 1] >> (16 * (rr & 1))) & 0xffffu);
-      v[rr] = ((wr >> lane) & 1u) ? gval<VDT>(vb + (pr + __popc(wr & lt)) * VB) : make_float2(0.f, 0.f);
+      v[rr] = (wr & lbit) ? gval<VDT>(vb + unsigned(pr + __popc(wr & lt)) * unsigned(VB)) : make_float2(0.f, 0.f);
     }
     if constexpr (DEGRID) {
       float ax = 0.f, ay = 0.f;
