@@ -84,3 +84,24 @@ def test_nonzero_proportion_follows_the_paper():
         frac.append(f)
         assert printed / 2 <= f <= printed * 2, (E, f, printed)
     assert frac[0] > frac[1] > frac[2]
+
+
+def test_linear_chirp_box_is_separable():
+    # exp(pi i w (l^2 + m^2)) = exp(pi i w l^2) exp(pi i w m^2): the kernel box of
+    # a paper-mode row (one tap at offset 0) is, up to one constant, the outer
+    # product g g^T with g[a] = f[-a mod G] and f the 1-D centred DFT of the axis
+    # chirp (what a separable build computes instead of a 2-D FFT)
+    N = 16
+    geo = O.paper_geometry(N, L)
+    G = geo.G
+    prob = synth.paper_problem(N, 0.1, seed=6)
+    lp = O.box_coords(G, geo.L, geo.extension)
+    for k in range(5):
+        u, v, w = prob.uvw[k]
+        K, _, _ = O.kernel_box(geo, u, v, w, G)
+        f = np.fft.fft(np.fft.ifftshift(O.chirp(lp, 0.0, w, "linear")))
+        g = f[(-np.arange(G)) % G]
+        P = np.outer(g, g)
+        c = K[0, 0] / P[0, 0]
+        assert abs(abs(c) - 1.0 / G ** 2) <= 1e-12 / G ** 2   # 1/G of the unitary 2-D DFT, 1/G of the box
+        assert np.allclose(K, c * P, rtol=0, atol=1e-12 * np.abs(K).max())
