@@ -51,7 +51,8 @@ def parse():
     ap.add_argument("--e", type=float, default=0.99)
     ap.add_argument("--value-dtype", default="f32", choices=["f32", "bf16", "f16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-rows", type=int, default=64)
+    ap.add_argument("--cpu-sample-rows", type=int, default=160,
+                    help="rows of the oracle sample timed as the CPU baseline (about 10 s of host work)")
     ap.add_argument("--workload", default="paper", choices=["paper", "precision", "batched", "learned", "spread"])
     ap.add_argument("--spread-seeds", type=int, default=3, help="spread workload: simulations per point")
     ap.add_argument("--spread-iters", type=int, default=200, help="spread workload: DR iterations")
