@@ -201,9 +201,10 @@ wproj_status wproj_build_kernels(wproj_plan *p, const double *uvw, int64_t m, do
  * attached to before the FFT: row k is FFT(chirp_k x A_{screen_id[k]}), convolved
  * with the gridding taps and thresholded like any other row.
  * wproj_set_screens: n_screens screens, complex64 [n_screens][G][G] row-major
- * (host or device; copied into the plan), sample (a, b) at
- * l = (a - G/2) L / N, m = (b - G/2) L / N over the padded field of view (image
- * pixel (p, q) at (p + N/2, q + N/2)).  n_screens = 0 drops them.  Non-finite
+ * (host or device; copied into the plan), sample (a, b) at the chirp's sample
+ * points l = (a - G/2) d, m = (b - G/2) d over the padded field of view, d = L/N
+ * (image pixel (p, q) at (p + N/2, q + N/2)); with upsampling = 1, d = L/(2N),
+ * the pixels of the upsampled image.  n_screens = 0 drops them.  Non-finite
  * samples -> WPROJ_ERR_INVALID_ARG.  Invalidates the current G.  Synchronous.
  * wproj_build_kernels_dde: as wproj_build_kernels with screen_id (device int32[m],
  * each in [0, n_screens), else WPROJ_ERR_INVALID_ARG) naming every row's screen.
