@@ -234,15 +234,23 @@ wproj_status wproj_phi_adj(wproj_plan *p, const void *y, float *x_re, void *x_cp
  * they run: programs whose device memory is reserved up front by another
  * runtime or pool allocator (a cudaMalloc there fails or escapes the pool's
  * accounting), and loops that cannot afford the device-wide synchronisation
- * cudaMalloc and cudaFree imply.  Its scratch (FFT intermediate, padded
- * spectrum, degridding partial sums) lives in one fixed array of 16 MiB that
- * every GPU loading this part of the library holds until the process exits;
- * plans whose scratch would exceed it (in practice N > 512) are rejected with
- * WPROJ_ERR_INVALID_ARG.  The first call on a device looks up that array's
- * device address; make that first call before any stream capture.  All calls
- * share the one array and leave their data in it: calls that overlap on the
- * GPU (other streams, other threads, other plans) race and must be serialised
- * by the caller.  x, y and the built G as for wproj_phi. */
+ * cudaMalloc and cudaFree imply.  Its scratch lives in one fixed array of
+ * 16 MiB that every GPU loading this part of the library holds until the
+ * process exits.  The scratch a plan needs is N*G + G*G complex values (FFT
+ * intermediate and padded spectrum) plus its degridding partial sums: one
+ * complex value per row piece of <= 16384 entries (COLUMNS) or four per
+ * (row, tile) segment (TILE_MASK), each part rounded up to 256 bytes; a plan
+ * whose total exceeds 16 MiB is rejected with WPROJ_ERR_INVALID_ARG.  So
+ * N = 512 fits up to 524,288 partial sums and N = 256 up to 1.7 million, while
+ * N = 256 with M = 32768 dense rows (8.4 million tile-stream segments) and any
+ * N >= 1024 are refused.  The first call on a device looks up that array's
+ * device address and keeps it for the process (a cudaDeviceReset invalidates
+ * it, as it invalidates every plan); make that first call before any stream
+ * capture.  All calls share the one array and leave their data in it: calls
+ * that overlap on the GPU (other streams, other threads, other plans) race and
+ * must be serialised by the caller.  Timing statistics (wproj_set_timing) are
+ * kept in the plan's host state, so two host threads calling on one plan with
+ * timing on race there too.  x, y and the built G as for wproj_phi. */
 wproj_status wproj_phi_noalloc(wproj_plan *p, const float *x, void *y, void *stream);
 
 /* Complex-image forward operator (for the adjoint identity): x_cplx N x N float2. */

@@ -14,7 +14,11 @@
 
 namespace {
 
-// 16 MiB per GPU: room for G <= 1024 (N <= 512) with up to ~500k row pieces.
+// 16 MiB per GPU.  A plan fits when N*G + G*G complex values (FFT intermediate
+// and padded spectrum) plus its degridding partial sums (one per row piece of
+// the column format, four per (row, tile) segment of the tile stream), each
+// part rounded up to 256 bytes, total at most this: N = 512 leaves room for
+// 524,288 partial sums, N = 256 for 1.7 million; N >= 1024 never fits.
 constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;
 constexpr int kMaxDevices = 64;
 
@@ -25,7 +29,9 @@ void *g_scratch_addr[kMaxDevices] = {nullptr};
 
 size_t round256(size_t n) { return (n + 255) & ~size_t(255); }
 
-// Device address of g_phi_scratch on the current device (looked up once per device).
+// Device address of g_phi_scratch on the current device (looked up once per
+// device and kept for the life of the process: a cudaDeviceReset, which also
+// invalidates every plan, invalidates it too).
 wproj_status scratch_address(void **out) {
   int dev = 0;
   WPROJ_CUDA(cudaGetDevice(&dev));
@@ -53,9 +59,10 @@ extern "C" wproj_status wproj_phi_noalloc(wproj_plan *p, const float *x, void *y
   const size_t n_part = round256(sizeof(float2) * size_t(degrid_partials(p)));
   const size_t need = n_inter + n_xt + n_part;
   if (need > kNoAllocScratchBytes)
-    return fail(WPROJ_ERR_INVALID_ARG, "phi_noalloc: this plan needs " + std::to_string(need) +
-                                           " bytes of scratch; the fixed limit is " +
-                                           std::to_string(kNoAllocScratchBytes) + " (N <= 512)");
+    return fail(WPROJ_ERR_INVALID_ARG,
+                "phi_noalloc: this plan needs " + std::to_string(need) + " bytes of scratch (" +
+                    std::to_string(degrid_partials(p)) + " degridding partial sums); the fixed limit is " +
+                    std::to_string(kNoAllocScratchBytes) + " bytes: N*G + G*G + partials complex values");
   void *base = nullptr;
   WPROJ_TRY(scratch_address(&base));
   unsigned char *b = static_cast<unsigned char *>(base);
@@ -63,6 +70,12 @@ extern "C" wproj_status wproj_phi_noalloc(wproj_plan *p, const float *x, void *y
   float2 *Xt = reinterpret_cast<float2 *>(b + n_inter);
   float2 *partial = reinterpret_cast<float2 *>(b + n_inter + n_xt);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  WPROJ_TRY(phi_forward_fft_into(p, x, inter, Xt, s));
+  {
+    // timed and counted like wproj_phi's two halves (FFT passes, then degridding)
+    ScopedTimer t(p, TC_FFT, s);
+    p->launches += p->g.upsampling ? 4 : 2;
+    WPROJ_TRY(phi_forward_fft_into(p, x, inter, Xt, s));
+  }
+  p->launches += 2;
   return degrid_into(p, Xt, partial, static_cast<float2 *>(y), s);
 }

@@ -192,6 +192,13 @@ def test_phi_and_adjoint_match_oracle_at_e1(wp, N, M, box, vdt):
     assert np.linalg.norm(xa - xa_ref) / np.linalg.norm(xa_ref) <= 1e-5
     xr = plan.phi_adj(torch.from_numpy(yv.astype(np.complex64)).to(dev())).cpu().numpy()
     assert np.linalg.norm(xr - xa_ref.real) / np.linalg.norm(xa_ref.real) <= 1e-5
+    if plan.csr().index_format == "mask":
+        # the tile-stream gridding split every tile's records over several chunks
+        # (>= 4096 entries each) whose partial tiles were summed: that path is the
+        # one compared element by element above
+        G = 2 * N
+        n_tiles = (G // min(32, G)) ** 2
+        assert plan.stats()["grid_chunks"] >= 2 * n_tiles
 
 
 def test_adjoint_identity_on_gpu(wp):

@@ -19,16 +19,34 @@ def _vp(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
-def test_phi_noalloc_matches_phi_on_consecutive_calls():
+# index formats (their partial-sum counts, and so the scratch layout, differ),
+# 16-bit values with row scales, and the paper's operator, whose upsampling
+# step uses the FFT slot of the scratch as 2 N^2 work
+CASES = [
+    dict(id="auto-f32", N=64, M=1229, kw={}),
+    dict(id="columns-f32", N=64, M=1229, kw=dict(index_format="columns")),
+    dict(id="mask-f32", N=64, M=600, kw=dict(index_format="mask")),
+    dict(id="columns-bf16", N=64, M=1229, kw=dict(index_format="columns", value_dtype="bf16")),
+    dict(id="mask-bf16", N=32, M=400, kw=dict(index_format="mask", value_dtype="bf16")),
+    dict(id="paper-mode", N=32, M=None, kw=dict(kb_support=1, chirp="linear", upsampling=True)),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c["id"] for c in CASES])
+def test_phi_noalloc_matches_phi_on_consecutive_calls(case):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_1307_3424_gb300 import synth, wproj
     dev = torch.device("cuda", torch.cuda.current_device())
     L = synth.fov_L()
-    N, M = 64, 1229
+    N = case["N"]
     rng = np.random.default_rng(11)
-    uvw = synth.random_uvw(rng, M, N, L, 1.0)
-    plan = wproj.Plan(N, L)
+    if case["M"] is None:
+        uvw = synth.paper_problem(N, 0.2, seed=2).uvw
+    else:
+        uvw = synth.random_uvw(rng, case["M"], N, L, 1.0)
+    M = uvw.shape[0]
+    plan = wproj.Plan(N, L, **case["kw"])
     plan.build_kernels(torch.from_numpy(uvw).to(dev), 0.99)
     lib = wproj.lib()
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
