@@ -53,14 +53,17 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-rows", type=int, default=512,
                     help="rows of the oracle sample timed on the host cores (a few seconds of host work)")
-    ap.add_argument("--workload", default="paper", choices=["paper", "precision", "batched", "learned", "spread"])
+    ap.add_argument("--workload", default="paper",
+                    choices=["paper", "precision", "batched", "learned", "spread", "build"])
     ap.add_argument("--spread-seeds", type=int, default=3, help="spread workload: simulations per point")
     ap.add_argument("--spread-iters", type=int, default=200, help="spread workload: DR iterations")
     ap.add_argument("--train-kernels", type=int, default=2 ** 20, help="learned workload: training kernels")
     ap.add_argument("--train-steps", type=int, default=1024, help="learned workload: Adam steps (batch 4096)")
     ap.add_argument("--batch-problems", type=int, default=None, help="problems of the batched workload")
     ap.add_argument("--no-plain", action="store_true", help="batched workload: skip the one-by-one comparison")
-    ap.add_argument("--index-format", default="auto", choices=["auto", "columns", "mask"])
+    ap.add_argument("--index-format", default="auto", choices=["auto", "columns", "mask", "runs"])
+    ap.add_argument("--build-workload", default="paper", choices=["paper", "precision"],
+                    help="build workload: the paper-scale case (or --n / --m) or the precision-form case")
     ap.add_argument("--n", type=int, default=None, help="image side of a smaller profiling case")
     ap.add_argument("--m", type=int, default=None, help="visibilities of a smaller profiling case")
     return ap.parse_args()
@@ -71,7 +74,10 @@ def workload(args):
     precision: N=1024, M=2^21, S(w) boxes), or a smaller case of the paper-scale
     recipe (profiling)."""
     if args.workload == "precision":
-        return synth.PRECISION
+        if args.m is None:
+            return synth.PRECISION
+        import dataclasses
+        return dataclasses.replace(synth.PRECISION, name=f"{synth.PRECISION.name}_m{args.m}", M=args.m)
     wl = synth.PAPER_SCALE
     if args.n is None and args.m is None:
         return wl
@@ -414,14 +420,21 @@ def run_ours(args):
     grid_ms = kst["t_grid_ms"] / max(1, kst["n_grid"])
     alg_deg = nnz * b_val + M * 8 + G * G * 8
     alg_grid = nnz * b_val + M * 8 + G * G * 8
-    # G as stored: values + column indices, or the tile-stream records
-    stored = nnz * (b_val + 4) if fmt == "columns" else stream_bytes
-    # kernel labels as in profiles/: k_stream<VDT, degrid?> for the tile stream
-    deg_name, grid_name = ("k_stream_degrid", "k_stream_grid") if fmt == "mask" else ("k_degrid", "k_grid")
-    if kst["t_degrid_ms"] >= kst["t_grid_ms"]:
-        dom, ms, alg, kname = "degrid", deg_ms, alg_deg, deg_name
+    # G as each operator reads it: values + column indices, the tile-stream
+    # records, or (run lengths) the row-major copy and the tile-major records
+    if fmt == "columns":
+        stored_deg = stored_grid = nnz * (b_val + 4)
+    elif fmt == "runs":
+        stored_deg, stored_grid = st["runs_bytes"], stream_bytes
     else:
-        dom, ms, alg, kname = "grid", grid_ms, alg_grid, grid_name
+        stored_deg = stored_grid = stream_bytes
+    # kernel labels as in profiles/
+    deg_name, grid_name = {"mask": ("k_stream_degrid", "k_stream_grid"), "runs": ("k_runs_degrid", "k_runs_grid"),
+                           "columns": ("k_degrid", "k_grid_cells")}[fmt]
+    if kst["t_degrid_ms"] >= kst["t_grid_ms"]:
+        dom, ms, alg, kname, stored = "degrid", deg_ms, alg_deg, deg_name, stored_deg
+    else:
+        dom, ms, alg, kname, stored = "grid", grid_ms, alg_grid, grid_name, stored_grid
     achieved = alg / (ms * 1e-3) / 1e9
     roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
             "frac": achieved / hbm_peak, "traffic": read_profile_traffic(kname),
@@ -431,7 +444,9 @@ def run_ours(args):
             "ms_per_launch": ms,
             "degrid_ms": deg_ms, "grid_ms": grid_ms,
             "degrid_frac": alg_deg / (deg_ms * 1e-3) / 1e9 / hbm_peak,
-            "grid_frac": alg_grid / (grid_ms * 1e-3) / 1e9 / hbm_peak}
+            "grid_frac": alg_grid / (grid_ms * 1e-3) / 1e9 / hbm_peak,
+            "degrid_as_stored_GBps": (stored_deg + M * 8 + G * G * 8) / (deg_ms * 1e-3) / 1e9,
+            "grid_as_stored_GBps": (stored_grid + M * 8 + G * G * 8) / (grid_ms * 1e-3) / 1e9}
 
     value = job_rate(PAIRS_PER_STEP * args.steps, ws, t_ms)
     e2e_value = job_rate(PAIRS_PER_STEP * args.steps, ws, t_e2e_ms)
@@ -444,7 +459,8 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(wl, e, {"nnz": nnz, "segments": n_seg, "G_bytes": stored, "index_format": fmt,
+            "config": workload_config(wl, e, {"nnz": nnz, "segments": n_seg, "G_bytes": stored_deg + (
+                                              stored_grid if fmt == "runs" else 0), "index_format": fmt,
                                               "value_dtype": args.value_dtype,
                                               "l2": "inputs larger than L2 (G exceeds L2 many times)",
                                               "parallelism": f"replicas x{ws}"}),
@@ -784,6 +800,71 @@ def run_spread(args):
     return 0
 
 
+def fp32_peak_tflops(peaks):
+    """FP32 (non-tensor) arithmetic peak: 152 SMs x 128 FP32 lanes x 2 flop per
+    FMA x the maximum SM clock."""
+    return 152 * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+
+
+def run_build(args):
+    """Part I alone (Sections 3.1-3.2): G of the paper-scale workload (or the
+    --n / --m case, or --build-workload precision) built `steps` times after
+    `warmup` builds.  Metric: w-kernels built per second over the wall time of
+    the builds (a build sizes G exactly and synchronises); the library's
+    CUDA-event timers give the device time of its stages (box tables + FFTs,
+    selection + per-tile counts, emission)."""
+    import torch
+    from paper_1307_3424_gb300 import wproj
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    wl = synth.PRECISION if args.build_workload == "precision" else workload(args)
+    e = args.e if args.build_workload != "precision" else wl.e
+    prob = synth.make_problem(wl, seed=0)
+    plan = wproj.Plan(wl.N, prob.L, value_dtype=args.value_dtype, box=wl.box, index_format=args.index_format)
+    uvw = torch.from_numpy(prob.uvw).to(dev)
+    for _ in range(max(1, args.warmup)):
+        plan.build_kernels(uvw, e)
+    torch.cuda.synchronize()
+    plan.set_timing(True)
+    plan.reset_stats()
+    clocks = ClockSampler(0)
+    clocks.start()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        plan.build_kernels(uvw, e)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    st = plan.stats()
+    plan.close()
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    M = wl.M
+    per = {k: st[f"t_build_{k}_ms"] / args.steps for k in ("fft", "select", "emit")}
+    roof = None
+    if wl.box == "G":
+        S = 2 * wl.N
+        fft_passes = st["n_build_fft"] / args.steps      # box batches transformed per build
+        flop = 2 * M * 5.0 * S * S * math.log2(S * S)    # two passes over every box per build
+        ach = flop / (per["fft"] * 1e-3) / 1e12
+        pk = fp32_peak_tflops(peaks)
+        roof = {"kernel": "k_box_rows + k_fft_cols (box tables and FFTs, both passes)", "bound": "alu",
+                "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk, "traffic": None,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                "flop_per_build": flop, "fft_ms_per_build": per["fft"], "batches_per_build": fft_passes}
+    line = {
+        "metric": "w_kernels_built_per_s", "value": M * args.steps / wall, "unit": "w-kernels/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(wl, e, {"nnz": st["nnz"], "box_min": st["box_min"], "box_max": st["box_max"],
+                                          "value_dtype": args.value_dtype}),
+        "stage_ms_per_build": per, "roofline": roof, "clocks": clk,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def snr_out_db(x, x_rec):
     """SNR_out = 20 log10(std(x) / std(x - x_rec)) (Section 4.1)."""
     return 20.0 * math.log10(float(np.std(x)) / float(np.std(np.asarray(x) - np.asarray(x_rec))))
@@ -804,6 +885,8 @@ def main():
         return run_learned(args)
     if args.workload == "spread":
         return run_spread(args)
+    if args.workload == "build":
+        return run_build(args)
     res = run_ours(args)
     out, kst = res
     if out is not None:

@@ -100,9 +100,32 @@ typedef struct {
  *                  count values in row-major cell order, zero-padded to 16 B
  *                (192 B of mask and prefixes per segment instead of 4 B per
  *                entry, and each tile's records contiguous for streaming).
- * AUTO picks TILE_MASK when segments average >= 256 entries (dense rows), COLUMNS
- * otherwise.  wproj_csr_rows exports any rows in CSR order from either format. */
-typedef enum { WPROJ_INDEX_AUTO = 0, WPROJ_INDEX_COLUMNS = 1, WPROJ_INDEX_TILE_MASK = 2 } wproj_index_format;
+ *   TILE_RUNS    run lengths, for plans whose kernel boxes are at most 64 x 64
+ *                cells (a small kernel keeps one contiguous run of cells per
+ *                grid row).  Every run is stored padded to an even length by one
+ *                zero value.  Two copies of the values:
+ *                  row-major, for the degridding: per row its window origin
+ *                  (j0 - S/2) mod G per axis, its runs in window order as uint32
+ *                  (window row | window column << 6 | (length - 1) << 12) and
+ *                  its values run after run;
+ *                  tile-major records, for the gridding: for every tile
+ *                  (ascending) and every row with entries in it (rows
+ *                  ascending), 16-byte aligned: int32 row, uint16 stored count,
+ *                  uint16 runs; the runs as uint16 (tile column | (length - 1)
+ *                  << 5 | tile row << 10), zero-padded to 16 B; the values
+ *                  (CSR order with the pads), zero-padded to 16 B.
+ *                (about 4 B per run instead of 4 B per entry).
+ * AUTO picks TILE_RUNS when every box is at most 64 x 64 cells (and the grid is
+ * at least 32 x 32), else TILE_MASK when segments average >= 256 entries (dense
+ * rows), else COLUMNS.  Requesting TILE_RUNS for larger boxes makes
+ * wproj_build_kernels return WPROJ_ERR_UNSUPPORTED.  wproj_csr_rows exports any
+ * rows in CSR order from every format. */
+typedef enum {
+  WPROJ_INDEX_AUTO = 0,
+  WPROJ_INDEX_COLUMNS = 1,
+  WPROJ_INDEX_TILE_MASK = 2,
+  WPROJ_INDEX_TILE_RUNS = 3
+} wproj_index_format;
 
 /* View of G held by a plan (device pointers owned by the plan; valid until the
  * next build or the plan's destruction). */
@@ -117,10 +140,10 @@ typedef struct {
   const float *row_scale;   /* m scales (bf16/f16: G[k, q] = row_scale[k] * stored value),
                                NULL for f32 */
   int32_t value_dtype;
-  int32_t index_format;     /* WPROJ_INDEX_COLUMNS or WPROJ_INDEX_TILE_MASK */
+  int32_t index_format;     /* WPROJ_INDEX_COLUMNS, WPROJ_INDEX_TILE_MASK or WPROJ_INDEX_TILE_RUNS */
   int64_t n_seg;            /* (row, tile) segments */
-  const void *stream;       /* TILE_MASK: the record stream; else NULL */
-  int64_t stream_bytes;     /* its size in bytes (0 for COLUMNS) */
+  const void *stream;       /* TILE_MASK / TILE_RUNS: the tile-major records; else NULL */
+  int64_t stream_bytes;     /* their size in bytes (0 for COLUMNS) */
 } wproj_csr;
 
 /* Entries of rows [k0, k1) of G in CSR order, whatever the index format:
@@ -170,6 +193,12 @@ typedef struct {
   double t_fft_ms, t_degrid_ms, t_grid_ms, t_reduce_ms, t_solver_ms;
   int64_t n_fft, n_degrid, n_grid, n_reduce, n_solver;
   int64_t launches;          /* kernels launched by Phi, Phi^H and the solver since the last reset */
+  int64_t runs_bytes;        /* TILE_RUNS: bytes of the row-major copy the degridding reads (values,
+                                runs, per-row offsets and origins); 0 for the other formats */
+  /* device time (ms) of the builds since the last reset when timing is on: box
+     tables and FFTs (both passes), selection and per-tile counts, emission */
+  double t_build_fft_ms, t_build_select_ms, t_build_emit_ms;
+  int64_t n_build_fft;       /* box batches transformed (each pass counts) */
 } wproj_stats;
 
 /* ---- plan ---------------------------------------------------------------- */

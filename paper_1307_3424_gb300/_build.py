@@ -22,7 +22,7 @@ OBJDIR = os.path.join(PKG, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", INCLUDE, "-I", CSRC]
-SOURCES = ["api.cu", "batch.cu", "build.cu", "cells.cu", "fft.cu", "gemm.cu", "mlp.cu", "noalloc.cu", "ops.cu", "scan.cu", "solve.cu", "tiles.cu", "wavelet.cu"]
+SOURCES = ["api.cu", "batch.cu", "build.cu", "cells.cu", "fft.cu", "gemm.cu", "mlp.cu", "noalloc.cu", "ops.cu", "runs.cu", "scan.cu", "solve.cu", "tiles.cu", "wavelet.cu"]
 
 
 def nvcc() -> str:

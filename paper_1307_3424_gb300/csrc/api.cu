@@ -80,10 +80,12 @@ ScopedTimer::ScopedTimer(wproj_plan *p_, int cls_, cudaStream_t s_) : p(p_), cls
   b = p->timer.get();
   if (a && b) cudaEventRecord(a, s);
 }
-ScopedTimer::~ScopedTimer() {
+ScopedTimer::~ScopedTimer() { stop(); }
+void ScopedTimer::stop() {
   if (!p->timing || !a || !b) return;
   cudaEventRecord(b, s);
   p->timer.pending.push_back({cls, {a, b}});
+  a = b = nullptr;
 }
 
 namespace {
@@ -149,7 +151,7 @@ wproj_status wproj_plan_create(wproj_plan **out, const wproj_grid_desc *d) {
   if (d->box != 0 && (!is_pow2(d->box) || d->box < 16 || d->box > G))
     return fail(WPROJ_ERR_INVALID_ARG, "box must be 0 or a power of two in [16, 2N]");
   if (d->value_dtype < 0 || d->value_dtype > 2) return fail(WPROJ_ERR_INVALID_ARG, "value_dtype must be 0, 1 or 2");
-  if (d->index_format < 0 || d->index_format > 2) return fail(WPROJ_ERR_INVALID_ARG, "index_format must be 0, 1 or 2");
+  if (d->index_format < 0 || d->index_format > 3) return fail(WPROJ_ERR_INVALID_ARG, "index_format must be 0, 1, 2 or 3");
   if (d->upsampling != 0 && d->upsampling != 1) return fail(WPROJ_ERR_INVALID_ARG, "upsampling must be 0 or 1");
   if (d->upsampling == 1 && d->kb_support != 1)
     return fail(WPROJ_ERR_INVALID_ARG, "upsampling = 1 (visibilities on the grid) needs kb_support = 1");
@@ -380,6 +382,13 @@ wproj_status wproj_get_stats(wproj_plan *p, wproj_stats *out) {
   out->n_reduce = p->timer.count[TC_REDUCE];
   out->n_solver = p->timer.count[TC_SOLVER];
   out->launches = p->launches;
+  out->t_build_fft_ms = p->timer.ms[TC_BFFT];
+  out->t_build_select_ms = p->timer.ms[TC_BSEL];
+  out->t_build_emit_ms = p->timer.ms[TC_BEMIT];
+  out->n_build_fft = p->timer.count[TC_BFFT];
+  out->runs_bytes = p->fmt == WPROJ_INDEX_TILE_RUNS
+                        ? p->rm_vals * (p->g.value_dtype == WPROJ_VAL_F32 ? 8 : 4) + p->rm_runs * 4 + p->m * 20
+                        : 0;
   return WPROJ_OK;
 }
 

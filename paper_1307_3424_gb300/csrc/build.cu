@@ -34,6 +34,10 @@ __host__ __device__ __forceinline__ int64_t i64max(int64_t a, int64_t b) { retur
 __host__ __device__ __forceinline__ int64_t i64min(int64_t a, int64_t b) { return a < b ? a : b; }
 
 constexpr size_t kBuildBatchBytes = size_t(128) << 20;   // kernel boxes in flight
+// (32 MB batches of 512^2 boxes, which stay in L2 between the passes, measured
+// slower: 866 against 638 ms for 32768 boxes; the selection's histogram
+// launches lose more parallelism than the L2 residency gains)
+size_t batch_bytes(int) { return kBuildBatchBytes; }
 constexpr int kMaxBatchBoxes = 16384;     // grid.y limit for per-box launches
 constexpr int kHistBins = 2048;
 constexpr int kSelChunk = 8192;          // entries per histogram block
@@ -489,31 +493,51 @@ k_tile_count(const float2 *__restrict__ K, int S, const int32_t *__restrict__ id
   }
 }
 
-// ties go to the earliest tiles (emission order); one thread per box
-__global__ void k_tie_alloc(int nb, const int32_t *__restrict__ ids, const int64_t *__restrict__ seg_base,
-                            const int32_t *__restrict__ ntile, const SelState *__restrict__ sel,
-                            const int32_t *__restrict__ cnt_gt, const int32_t *__restrict__ cnt_eq,
-                            int32_t *__restrict__ seg_cnt, int32_t *__restrict__ seg_tieb,
-                            uint32_t *__restrict__ r_thr, int32_t *__restrict__ r_ntie,
-                            int8_t *__restrict__ r_all, float *__restrict__ r_max) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= nb) return;
+// ties go to the earliest tiles (emission order): tile i of a box takes
+// min(eq_i, n_tie - sum_{j<i} eq_j) of its threshold ties; one block per box
+__global__ void __launch_bounds__(128)
+k_tie_alloc(const int32_t *__restrict__ ids, const int64_t *__restrict__ seg_base,
+            const int32_t *__restrict__ ntile, const SelState *__restrict__ sel,
+            const int32_t *__restrict__ cnt_gt, const int32_t *__restrict__ cnt_eq,
+            int32_t *__restrict__ seg_cnt, int32_t *__restrict__ seg_tieb,
+            uint32_t *__restrict__ r_thr, int32_t *__restrict__ r_ntie,
+            int8_t *__restrict__ r_all, float *__restrict__ r_max) {
+  __shared__ int wsum[4];
+  const int b = blockIdx.x;
   const int k = ids[b];
   const SelState st = sel[b];
   const int64_t base = seg_base[k];
   const int nt = ntile[k];
-  int rem = st.all ? 0 : st.n_tie;
-  for (int i = 0; i < nt; ++i) {
-    const int e = st.all ? 0 : cnt_eq[base + i];
-    const int a = min(e, rem);
-    seg_tieb[base + i] = (st.all ? 0 : st.n_tie) - rem;
-    rem -= a;
-    seg_cnt[base + i] = cnt_gt[base + i] + a;
+  const int ntie = st.all ? 0 : st.n_tie;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int carry = 0;   // ties of the tiles before this group of 128
+  for (int i0 = 0; i0 < nt; i0 += 128) {
+    const int i = i0 + threadIdx.x;
+    const int e = (i < nt && !st.all) ? cnt_eq[base + i] : 0;
+    int inc = e;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int n = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += n;
+    }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    int before = carry;
+    for (int j = 0; j < w; ++j) before += wsum[j];
+    const int excl = before + inc - e;
+    if (i < nt) {
+      const int a = min(e, max(0, ntie - excl));
+      seg_tieb[base + i] = min(excl, ntie);
+      seg_cnt[base + i] = cnt_gt[base + i] + a;
+    }
+    carry += wsum[0] + wsum[1] + wsum[2] + wsum[3];
+    __syncthreads();
   }
-  r_thr[k] = st.thr_key;
-  r_ntie[k] = st.n_tie;
-  r_all[k] = int8_t(st.all);
-  r_max[k] = sqrtf(__uint_as_float(st.maxkey));
+  if (threadIdx.x == 0) {
+    r_thr[k] = st.thr_key;
+    r_ntie[k] = st.n_tie;
+    r_all[k] = int8_t(st.all);
+    r_max[k] = sqrtf(__uint_as_float(st.maxkey));
+  }
 }
 
 // ---- emission -------------------------------------------------------------------------
@@ -919,7 +943,7 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
     p->box_max = std::max(p->box_max, S);
     const int64_t per = int64_t(S) * S * sizeof(float2);
     max_nb = std::max<int>(max_nb, (int)std::min<int64_t>(std::min<int64_t>(cls_ptr[c + 1] - cls_ptr[c], kMaxBatchBoxes),
-                                                            std::max<int64_t>(1, kBuildBatchBytes / per)));
+                                                            std::max<int64_t>(1, batch_bytes(S) / per)));
   }
   DevBuf Kbuf, Au, Av, bmode, bwf, bwd, bsel, hcnt, hq, lcoord, lsq, bsid;
   WPROJ_TRY(Kbuf.alloc(std::max<size_t>(kBuildBatchBytes, size_t(p->box_max) * p->box_max * sizeof(float2))));
@@ -940,6 +964,7 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
   const int vb = vdt == WPROJ_VAL_F32 ? 8 : 4;
   const int n_tiles = g.nT * g.nT;
   DevBuf tile_seg, tptr;
+  bool want_runs = false;   // TILE_RUNS: emitted as columns, then transcoded
 
   for (int phase = 1; phase <= 2; ++phase) {
     if (phase == 2) {
@@ -957,9 +982,19 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
       // spend per-segment work on all 32 tile rows); measured at N=256/M=32768
       // (573 entries per segment: masks 1.5x faster) and N=1024/M=2^21 (41 per
       // segment: columns 5x faster)
+      // boxes of at most 64 x 64 cells keep one run of cells per grid row: run
+      // descriptors (TILE_RUNS) then cost a few per cent of the value bytes
+      // (measured at N=1024/M=2^21: 283 entries in 16.6 runs per row)
+      const bool runs_ok = p->box_max <= 64 && g.tile == 32;
       int fmt = g.index_format;
-      if (fmt == WPROJ_INDEX_AUTO) fmt = (p->nnz >= 256 * n_seg) ? WPROJ_INDEX_TILE_MASK : WPROJ_INDEX_COLUMNS;
+      if (fmt == WPROJ_INDEX_AUTO)
+        fmt = runs_ok ? WPROJ_INDEX_TILE_RUNS
+                      : ((p->nnz >= 256 * n_seg) ? WPROJ_INDEX_TILE_MASK : WPROJ_INDEX_COLUMNS);
+      if (fmt == WPROJ_INDEX_TILE_RUNS && !runs_ok)
+        return fail(WPROJ_ERR_UNSUPPORTED, "build_kernels: TILE_RUNS needs kernel boxes of at most 64 x 64 cells");
       if (g.tile != 32) fmt = WPROJ_INDEX_COLUMNS;
+      want_runs = fmt == WPROJ_INDEX_TILE_RUNS;
+      if (want_runs) fmt = WPROJ_INDEX_COLUMNS;
       p->fmt = fmt;
       // segments in tile order, rows ascending inside a tile: the gridding's
       // order, and the record order of the tile stream
@@ -1013,13 +1048,14 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
       const int S = 16 << c;
       const int64_t per = int64_t(S) * S;
       const int nbmax = (int)std::min<int64_t>(std::min<int64_t>(ghi - glo, kMaxBatchBoxes),
-                                               std::max<int64_t>(1, kBuildBatchBytes / (per * 8)));
+                                               std::max<int64_t>(1, batch_bytes(S) / (per * 8)));
       k_coord_tables<<<ceil_div(S, 256), 256, 0, s>>>(S, g.L, g.extension == WPROJ_EXT_CLAMP,
                                                       lcoord.as<double>(), lsq.as<float>());
       WPROJ_CHECK_LAUNCH("coord tables");
       for (int64_t b0 = glo; b0 < ghi; b0 += nbmax) {
         const int nb = (int)std::min<int64_t>(nbmax, ghi - b0);
         const int32_t *ids = d_ids.as<int32_t>() + b0;
+        ScopedTimer t_fft(p, TC_BFFT, s);
         k_box_tables<<<nb, 128, 0, s>>>(ids, uvw, d_delta.as<double2>(), g, S, lcoord.as<double>(),
                                         Au.as<float2>(), Av.as<float2>(), bmode.as<int8_t>(),
                                         bwf.as<float>(), bwd.as<double>(), bsel.as<SelState>(), sid,
@@ -1036,8 +1072,10 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
           bb.bsid = bsid.as<int32_t>();
         }
         WPROJ_TRY(box_fft(p, bb, s));
+        t_fft.stop();
         const dim3 hgrid(ceil_div(per, kSelChunk), nb);
         if (phase == 1) {
+          ScopedTimer t_sel(p, TC_BSEL, s);
           WPROJ_CUDA(cudaMemsetAsync(hcnt.ptr, 0, sizeof(unsigned) * kHistBins * nb, s));
           WPROJ_CUDA(cudaMemsetAsync(hq.ptr, 0, sizeof(unsigned long long) * kHistBins * nb, s));
           k_sel_hist<0><<<hgrid, 256, 0, s>>>(bb.K, S, bsel.as<SelState>(), hcnt.as<unsigned>(), hq.as<unsigned long long>());
@@ -1061,13 +1099,14 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
                                                 bsel.as<SelState>(), d_cntgt.as<int32_t>(), d_cnteq.as<int32_t>(),
                                                 smem_tiles);
           WPROJ_CHECK_LAUNCH("tile count");
-          k_tie_alloc<<<ceil_div(nb, 128), 128, 0, s>>>(nb, ids, d_segbase.as<int64_t>(), d_ntile.as<int32_t>(),
+          k_tie_alloc<<<nb, 128, 0, s>>>(ids, d_segbase.as<int64_t>(), d_ntile.as<int32_t>(),
                                                        bsel.as<SelState>(), d_cntgt.as<int32_t>(),
                                                        d_cnteq.as<int32_t>(), p->seg_cnt.as<int32_t>(),
                                                        d_tieb.as<int32_t>(), r_thr.as<uint32_t>(),
                                                        r_ntie.as<int32_t>(), r_all.as<int8_t>(), r_max.as<float>());
           WPROJ_CHECK_LAUNCH("tie alloc");
         } else {
+          ScopedTimer t_emit(p, TC_BEMIT, s);
           const int gx = std::min(box_tiles(S, g), 1024);   // the kernel strides over more
           k_emit<<<dim3(gx, nb), 256, 0, s>>>(bb.K, S, ids, d_j0.as<int2>(), d_segbase.as<int64_t>(),
                                               d_ntile.as<int32_t>(), g, p->seg_off.as<int64_t>(),
@@ -1088,9 +1127,29 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
   } else {
     p->row_scale.release();
   }
+  if (want_runs) {
+    p->m = m;
+    p->n_seg = n_seg;
+    WPROJ_TRY(build_runs(p, d_j0.as<int2>(), d_Sk.as<int32_t>(), tile_seg.as<int32_t>(), s));
+    p->fmt = WPROJ_INDEX_TILE_RUNS;
+  } else {
+    p->rm_vptr.release();
+    p->rm_rptr.release();
+    p->rm_org.release();
+    p->rm_run.release();
+    p->rm_val.release();
+    p->rm_runs = p->rm_vals = 0;
+  }
 
   // ---- degridding: row pieces (COLUMNS) or one partial per (segment, warp) (TILE_MASK)
-  if (p->fmt == WPROJ_INDEX_TILE_MASK) {
+  if (p->fmt == WPROJ_INDEX_TILE_RUNS) {
+    p->n_pieces = 0;
+    p->piece_row.release();
+    p->piece_lo.release();
+    p->piece_len.release();
+    p->row_piece_ptr.release();
+    WPROJ_TRY(p->piece_partial.alloc(sizeof(float2)));
+  } else if (p->fmt == WPROJ_INDEX_TILE_MASK) {
     p->n_pieces = 0;
     p->piece_row.release();
     p->piece_lo.release();
@@ -1105,7 +1164,7 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
 
   // ---- gridding: chunks of one tile's segments (tile order), balanced by entries
   {
-    const bool rec = p->fmt == WPROJ_INDEX_TILE_MASK;
+    const bool rec = p->fmt == WPROJ_INDEX_TILE_MASK || p->fmt == WPROJ_INDEX_TILE_RUNS;
     const int64_t chunk = grid_chunk(p->nnz);
     DevBuf cntsorted, cum;
     WPROJ_TRY(cntsorted.alloc(sizeof(int32_t) * std::max<int64_t>(1, n_seg)));

@@ -204,7 +204,7 @@ wproj_status launch_degrid_cols(wproj_plan *p, const float2 *Xt, float2 *partial
 }  // namespace
 
 wproj_status degrid(wproj_plan *p, const float2 *Xt, float2 *y, cudaStream_t s) {
-  p->launches += 2;
+  p->launches += p->fmt == WPROJ_INDEX_TILE_RUNS ? 1 : 2;
   return degrid_into(p, Xt, p->piece_partial.as<float2>(), y, s);
 }
 
@@ -212,6 +212,10 @@ wproj_status degrid(wproj_plan *p, const float2 *Xt, float2 *y, cudaStream_t s) 
 // (degrid_partials(p) float2); the kernels and their launch shape are those of
 // degrid().
 wproj_status degrid_into(wproj_plan *p, const float2 *Xt, float2 *partial, float2 *y, cudaStream_t s) {
+  if (p->fmt == WPROJ_INDEX_TILE_RUNS) {   // warp per row, no partial sums
+    ScopedTimer t(p, TC_DEGRID, s);
+    return degrid_runs(p, Xt, y, s);
+  }
   {
     ScopedTimer t(p, TC_DEGRID, s);
     if (p->fmt == WPROJ_INDEX_TILE_MASK) WPROJ_TRY(degrid_stream(p, Xt, partial, s));
@@ -226,6 +230,7 @@ wproj_status degrid_into(wproj_plan *p, const float2 *Xt, float2 *partial, float
 }
 
 int64_t degrid_partials(const wproj_plan *p) {
+  if (p->fmt == WPROJ_INDEX_TILE_RUNS) return 0;
   return p->fmt == WPROJ_INDEX_TILE_MASK ? degrid_stream_partials(p) : p->n_pieces;
 }
 
@@ -245,7 +250,12 @@ wproj_status grid(wproj_plan *p, const float2 *y, float2 *Xt2, cudaStream_t s) {
         p->seg_meta.as<SegMeta>(), p->col.as<int32_t>(), p->val.ptr, rs, y, logG, g.tile, g.nT, nullptr,    \
         nullptr, p->grid_partial.as<float2>());                                                             \
   } while (0)
-    if (p->fmt == WPROJ_INDEX_TILE_MASK) {
+    if (p->fmt == WPROJ_INDEX_TILE_RUNS) {
+      int nl = 0;
+      WPROJ_TRY(grid_runs(p, y, Xt2, &nl, s));
+      p->launches += nl - 2;
+      return WPROJ_OK;
+    } else if (p->fmt == WPROJ_INDEX_TILE_MASK) {
       WPROJ_TRY(grid_stream(p, y, s));
     } else if (p->has_cells) {
       p->launches -= 1;   // one kernel, no chunk reduction
@@ -270,6 +280,7 @@ wproj_status grid(wproj_plan *p, const float2 *y, float2 *Xt2, cudaStream_t s) {
 wproj_status csr_rows(const wproj_plan *p, int64_t k0, int64_t k1, int32_t *col_out, void *val_out,
                       cudaStream_t s) {
   if (p->fmt == WPROJ_INDEX_TILE_MASK) return stream_export(p, k0, k1, col_out, val_out, s);
+  if (p->fmt == WPROJ_INDEX_TILE_RUNS) return runs_export(p, k0, k1, col_out, val_out, s);
   int64_t r[2] = {0, 0};
   WPROJ_CUDA(cudaMemcpyAsync(&r[0], p->row_ptr.as<int64_t>() + k0, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   WPROJ_CUDA(cudaMemcpyAsync(&r[1], p->row_ptr.as<int64_t>() + k1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));

@@ -71,7 +71,8 @@ struct BatchOps {
 };
 
 // Timing accumulator for one class of kernels.
-enum TimerClass { TC_FFT = 0, TC_DEGRID, TC_GRID, TC_REDUCE, TC_SOLVER, TC_COUNT };
+// (TC_B*: the kernel build: box tables + box FFTs, selection + counts, emission)
+enum TimerClass { TC_FFT = 0, TC_DEGRID, TC_GRID, TC_REDUCE, TC_SOLVER, TC_BFFT, TC_BSEL, TC_BEMIT, TC_COUNT };
 
 struct EventTimer {
   std::vector<cudaEvent_t> pool;
@@ -118,6 +119,14 @@ struct wproj_plan {
   wproj::DevBuf seg_rec;     // int64[n_seg] byte offset of each segment's record (TILE_MASK)
   wproj::DevBuf rec_off;     // int64[n_seg+1] byte offset of the records in stream order (TILE_MASK)
   wproj::DevBuf seg_tile;    // int32[n_seg] tile index of each segment
+  // TILE_RUNS: the row-major copy of the degridding (runs padded to even lengths);
+  // the tile-major records of the gridding live in `stream` / `rec_off` / `seg_rec`
+  int64_t rm_runs = 0, rm_vals = 0;
+  wproj::DevBuf rm_vptr;     // int64[m+1] first stored value of each row
+  wproj::DevBuf rm_rptr;     // int64[m+1] first run of each row
+  wproj::DevBuf rm_org;      // uint32[m] window origin (j0 - S/2) mod G: u | v << 16
+  wproj::DevBuf rm_run;      // uint32[rm_runs] window row | window column << 6 | (length - 1) << 12
+  wproj::DevBuf rm_val;      // values[rm_vals]
   wproj::DevBuf seg_base;    // int64[m+1] first segment of each row
 
   // segments: one per (row, touched tile), ordered by row then tile
@@ -183,6 +192,7 @@ struct ScopedTimer {
   cudaEvent_t a = nullptr, b = nullptr;
   ScopedTimer(wproj_plan *p_, int cls_, cudaStream_t s_);
   ~ScopedTimer();
+  void stop();   // end the interval now (the destructor then does nothing)
 };
 
 // fft.cu
@@ -260,6 +270,14 @@ wproj_status grid(wproj_plan *p, const float2 *y, float2 *Xt2, cudaStream_t s);
 wproj_status apply_phi(wproj_plan *p, const float *x, const float2 *xc, float2 *y, cudaStream_t s);
 wproj_status apply_phi_adj(wproj_plan *p, const float2 *y, float *x_re, float2 *x_cplx,
                            const float *z, int mode, cudaStream_t s);
+
+// runs.cu (TILE_RUNS format): both copies from the column form in col / val, which
+// is then released; tile_seg = segments in tile order
+wproj_status build_runs(wproj_plan *p, const int2 *j0, const int32_t *Sk, const int32_t *tile_seg, cudaStream_t s);
+wproj_status degrid_runs(wproj_plan *p, const float2 *Xt, float2 *y, cudaStream_t s);
+wproj_status grid_runs(wproj_plan *p, const float2 *y, float2 *Xt2, int *launches, cudaStream_t s);
+wproj_status runs_export(const wproj_plan *p, int64_t k0, int64_t k1, int32_t *col_out, void *val_out,
+                         cudaStream_t s);
 
 // build.cu: work units shared by plans and batches
 // row pieces of <= piece entries (m rows, row_ptr[m+1])

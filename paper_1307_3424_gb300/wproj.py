@@ -20,7 +20,7 @@ OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NOT_BUILT, ERR_UNSUPPOR
 CHIRP = {"exact": 0, "linear": 1}
 EXTENSION = {"full": 0, "clamp": 1}
 VALUE_DTYPE = {"f32": 0, "bf16": 1, "f16": 2}
-INDEX_FORMAT = {"auto": 0, "columns": 1, "mask": 2}
+INDEX_FORMAT = {"auto": 0, "columns": 1, "mask": 2, "runs": 3}
 
 EXPORTED = [
     "wproj_plan_create", "wproj_plan_destroy", "wproj_build_kernels", "wproj_get_csr",
@@ -96,7 +96,9 @@ class Stats(ctypes.Structure):
                 ("t_reduce_ms", ctypes.c_double), ("t_solver_ms", ctypes.c_double),
                 ("n_fft", ctypes.c_int64), ("n_degrid", ctypes.c_int64), ("n_grid", ctypes.c_int64),
                 ("n_reduce", ctypes.c_int64), ("n_solver", ctypes.c_int64),
-                ("launches", ctypes.c_int64)]
+                ("launches", ctypes.c_int64), ("runs_bytes", ctypes.c_int64), ("t_build_fft_ms", ctypes.c_double),
+                ("t_build_select_ms", ctypes.c_double), ("t_build_emit_ms", ctypes.c_double),
+                ("n_build_fft", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -220,7 +222,7 @@ class CSRView:
         self._plan = plan
         self.m, self.nnz, self.n_cols, self.n_seg = int(c.m), int(c.nnz), int(c.n_cols), int(c.n_seg)
         self.value_dtype = {0: "f32", 1: "bf16", 2: "f16"}[c.value_dtype]
-        self.index_format = {1: "columns", 2: "mask"}[c.index_format]
+        self.index_format = {1: "columns", 2: "mask", 3: "runs"}[c.index_format]
         self.stream_bytes = int(c.stream_bytes)
         self._dev = torch.device("cuda", torch.cuda.current_device())
         self.row_ptr = torch.as_tensor(_CAI(c.row_ptr, (self.m + 1,), "<i8"), device=self._dev)

@@ -47,7 +47,7 @@ def gpu_plan(wp, N, uvw, screens, sid, e, fmt="columns", vdt="f32"):
     return plan
 
 
-@pytest.mark.parametrize("N,fmt", [(16, "columns"), (32, "columns"), (32, "mask")])
+@pytest.mark.parametrize("N,fmt", [(16, "columns"), (32, "columns"), (32, "mask"), (16, "runs"), (32, "runs")])
 def test_operators_with_screens_match_oracle_at_e1(wp, N, fmt):
     uvw, screens, sid = problem(N, 150, 4, N)
     geo = O.Geometry(N, L)

@@ -42,7 +42,7 @@ def test_operators_match_the_definition_at_E1(wp, N, cov):
     x = rng.standard_normal((N, N))
     M = prob.uvw.shape[0]
     yv = rng.standard_normal(M) + 1j * rng.standard_normal(M)
-    for fmt in ("columns", "mask"):
+    for fmt in ("columns", "mask", "runs"):     # G = 2N <= 64: run lengths apply
         plan = paper_plan(wp, N, fmt)
         plan.build_kernels(torch.from_numpy(prob.uvw).to(dev()), 1.0)
         y = plan.phi(torch.from_numpy(x.astype(np.float32)).to(dev())).cpu().numpy()

@@ -166,6 +166,11 @@ def test_build_rejects_bad_input(wp):
     with pytest.raises(wp.WprojError) as ei:
         plan.phi(torch.zeros((N, N), device=dev()))
     assert ei.value.status == wp.ERR_NOT_BUILT
+    # run lengths need boxes of at most 64 x 64 cells (here S = G = 128)
+    big = wp.Plan(64, L, index_format="runs")
+    with pytest.raises(wp.WprojError) as ei:
+        big.build_kernels(torch.zeros((2, 3), dtype=torch.float64, device=dev()), 0.99)
+    assert ei.value.status == wp.ERR_UNSUPPORTED
 
 
 # ---- operators ------------------------------------------------------------------------
@@ -245,10 +250,14 @@ def test_bf16_and_f16_values(wp):
 
 
 @pytest.mark.parametrize("N,M,e,box,vdt", [(32, 200, 1.0, None, "f32"), (64, 150, 0.99, None, "f32"),
-                                           (64, 120, 0.99, None, "bf16"), (128, 60, 0.9, "rule", "f32")])
+                                           (64, 120, 0.99, None, "bf16"), (128, 60, 0.9, "rule", "f32"),
+                                           (64, 300, 0.99, 32, "f32"), (64, 250, 1.0, 64, "f32"),
+                                           (64, 200, 0.95, 64, "bf16"), (32, 150, 0.9, None, "f16"),
+                                           (128, 400, 0.99, 32, "bf16")])
 def test_index_formats_build_and_operators(wp, N, M, e, box, vdt):
-    # the two column storages hold the same G (each checked against the oracle)
-    # and give the same operators; at e = 1 both match the oracle's operators
+    # the column storages hold the same G (each checked against the oracle) and
+    # give the same operators; at e = 1 all match the oracle's operators.  Run
+    # lengths apply when every box is at most 64 x 64 cells.
     rng = np.random.default_rng(N + M + 1)
     uvw = synth.random_uvw(rng, M, N, L, 1.0)
     geo = O.Geometry(N, L)
@@ -257,7 +266,9 @@ def test_index_formats_build_and_operators(wp, N, M, e, box, vdt):
     xg = torch.from_numpy(x.astype(np.float32)).to(dev())
     yg = torch.from_numpy(yv.astype(np.complex64)).to(dev())
     out, exported = {}, {}
-    for fmt in ("columns", "mask"):
+    S = 2 * N if box is None else (box if box != "rule" else 2 * N)
+    fmts = ("columns", "mask", "runs") if S <= 64 else ("columns", "mask")
+    for fmt in fmts:
         plan = wp.Plan(N, L, box=box or "G", value_dtype=vdt, index_format=fmt)
         plan.build_kernels(torch.from_numpy(uvw).to(dev()), e)
         c = plan.csr()
@@ -275,10 +286,11 @@ def test_index_formats_build_and_operators(wp, N, M, e, box, vdt):
         exported[fmt] = (col, val)
         plan.close()
     # the same G: identical columns and stored values in CSR order
-    assert torch.equal(exported["columns"][0], exported["mask"][0])
-    assert torch.equal(exported["columns"][1], exported["mask"][1])
-    for a, b in zip(out["columns"], out["mask"]):
-        assert np.linalg.norm(a - b) <= 1e-6 * np.linalg.norm(a)
+    for fmt in fmts[1:]:
+        assert torch.equal(exported["columns"][0], exported[fmt][0])
+        assert torch.equal(exported["columns"][1], exported[fmt][1])
+        for a, b in zip(out["columns"], out[fmt]):
+            assert np.linalg.norm(a - b) <= 1e-6 * np.linalg.norm(a)
     if e == 1.0 and vdt == "f32":
         Gm = O.build_G(geo, uvw, 1.0, S=box)
         y_ref, xa_ref = O.phi(geo, Gm, x), O.phi_adj(geo, Gm, yv)

@@ -56,6 +56,7 @@ def test_precision_form_against_oracle(case, vdt):
     plan = wp.Plan(wl.N, prob.L, box="rule", value_dtype=vdt)
     plan.build_kernels(torch.from_numpy(prob.uvw).to(dev), wl.e)
     c = plan.csr()
+    assert c.index_format == "runs"     # boxes of 32 and 64 cells: run lengths
     G = geo.G
     num = den = 0.0
     for k in case["rows"]:

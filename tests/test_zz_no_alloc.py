@@ -29,6 +29,8 @@ CASES = [
     dict(id="columns-bf16", N=64, M=1229, kw=dict(index_format="columns", value_dtype="bf16")),
     dict(id="mask-bf16", N=32, M=400, kw=dict(index_format="mask", value_dtype="bf16")),
     dict(id="paper-mode", N=32, M=None, kw=dict(kb_support=1, chirp="linear", upsampling=True)),
+    dict(id="runs-f32", N=32, M=500, kw=dict(index_format="runs")),
+    dict(id="runs-bf16", N=64, M=800, kw=dict(index_format="runs", value_dtype="bf16", box=32)),
 ]
 
 
