@@ -361,6 +361,14 @@ const char *wproj_version(void);
  * dense contraction of the learned-kernel MLP, exported for testing.
  * m, n multiples of 128, k a multiple of 64, else WPROJ_ERR_INVALID_ARG.
  * bias may be NULL.  Synchronous; WPROJ_ERR_TIMEOUT if a tensor-core wait ran out. */
+/* Test hook of the GEMM's bounded waits (no counterpart in the paper; failure
+ * detection).  wait_on_unset_barrier != 0 makes every later wproj_gemm_bf16 CTA
+ * first wait on an mbarrier that nothing arrives on, for at most limit_ns
+ * nanoseconds (0 = the normal limit of 2 s): the call then returns
+ * WPROJ_ERR_TIMEOUT after each CTA has drained its committed MMAs and freed its
+ * tensor memory, and the context stays usable.  (0, 0) restores normal
+ * operation.  Affects the current device; synchronous. */
+wproj_status wproj_gemm_test_hook(int32_t wait_on_unset_barrier, uint64_t limit_ns);
 wproj_status wproj_gemm_bf16(int32_t m, int32_t n, int32_t k, const void *a, const void *b, const float *bias,
                              void *c, int32_t out_bf16, void *stream);
 

@@ -946,7 +946,24 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
                                                             std::max<int64_t>(1, batch_bytes(S) / per)));
   }
   DevBuf Kbuf, Au, Av, bmode, bwf, bwd, bsel, hcnt, hq, lcoord, lsq, bsid;
-  WPROJ_TRY(Kbuf.alloc(std::max<size_t>(kBuildBatchBytes, size_t(p->box_max) * p->box_max * sizeof(float2))));
+  // Pass 2 needs every box's transform again.  When the device has room for all
+  // of them (and, with a margin, for G, whose size is at most 1.5x theirs), pass
+  // 1 keeps them and pass 2 emits without recomputing the tables and FFTs;
+  // otherwise pass 2 recomputes them batch by batch.
+  int64_t k_total = 0;
+  for (int c = 0; c < 9; ++c) k_total += (cls_ptr[c + 1] - cls_ptr[c]) * int64_t(16 << c) * (16 << c) * int64_t(sizeof(float2));
+  DevBuf Kall;
+  bool keep_all = false;
+  {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess &&
+        double(free_b) > 2.5 * double(k_total) + double(size_t(2) << 30)) {
+      keep_all = Kall.alloc(size_t(k_total)) == WPROJ_OK;
+      if (!keep_all) cudaGetLastError();   // fall back to recomputing
+    }
+  }
+  if (!keep_all)
+    WPROJ_TRY(Kbuf.alloc(std::max<size_t>(kBuildBatchBytes, size_t(p->box_max) * p->box_max * sizeof(float2))));
   WPROJ_TRY(Au.alloc(sizeof(float2) * size_t(max_nb) * p->box_max));
   WPROJ_TRY(Av.alloc(sizeof(float2) * size_t(max_nb) * p->box_max));
   WPROJ_TRY(bmode.alloc(max_nb));
@@ -965,8 +982,10 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
   const int n_tiles = g.nT * g.nT;
   DevBuf tile_seg, tptr;
   bool want_runs = false;   // TILE_RUNS: emitted as columns, then transcoded
+  int64_t n_rec = 0;        // TILE_RUNS: records (segments holding entries), tile order
 
   for (int phase = 1; phase <= 2; ++phase) {
+    int64_t koff = 0;   // boxes transformed so far (position in Kall)
     if (phase == 2) {
       // lay out G exactly
       WPROJ_TRY(exclusive_scan_i32_to_i64(p->seg_cnt.as<int32_t>(), p->seg_off.as<int64_t>(), n_seg, s));
@@ -1055,23 +1074,28 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
       for (int64_t b0 = glo; b0 < ghi; b0 += nbmax) {
         const int nb = (int)std::min<int64_t>(nbmax, ghi - b0);
         const int32_t *ids = d_ids.as<int32_t>() + b0;
-        ScopedTimer t_fft(p, TC_BFFT, s);
-        k_box_tables<<<nb, 128, 0, s>>>(ids, uvw, d_delta.as<double2>(), g, S, lcoord.as<double>(),
-                                        Au.as<float2>(), Av.as<float2>(), bmode.as<int8_t>(),
-                                        bwf.as<float>(), bwd.as<double>(), bsel.as<SelState>(), sid,
-                                        sid ? p->screen_max2.as<float>() : nullptr, bsid.as<int32_t>());
-        WPROJ_CHECK_LAUNCH("box tables");
+        float2 *Kb = keep_all ? Kall.as<float2>() + koff : Kbuf.as<float2>();
+        koff += int64_t(nb) * per;
         BoxBatch bb;
         bb.S = S; bb.nb = nb;
-        bb.Au = Au.as<float2>(); bb.Av = Av.as<float2>();
-        bb.mode = bmode.as<int8_t>(); bb.wf = bwf.as<float>(); bb.wd = bwd.as<double>();
-        bb.lsq = lsq.as<float>(); bb.lcoord = lcoord.as<double>();
-        bb.K = Kbuf.as<float2>();
-        if (sid) {
-          bb.screens = p->screens.as<float2>();
-          bb.bsid = bsid.as<int32_t>();
+        bb.K = Kb;
+        const bool transform = phase == 1 || !keep_all;
+        ScopedTimer t_fft(p, TC_BFFT, s);
+        if (transform) {
+          k_box_tables<<<nb, 128, 0, s>>>(ids, uvw, d_delta.as<double2>(), g, S, lcoord.as<double>(),
+                                          Au.as<float2>(), Av.as<float2>(), bmode.as<int8_t>(),
+                                          bwf.as<float>(), bwd.as<double>(), bsel.as<SelState>(), sid,
+                                          sid ? p->screen_max2.as<float>() : nullptr, bsid.as<int32_t>());
+          WPROJ_CHECK_LAUNCH("box tables");
+          bb.Au = Au.as<float2>(); bb.Av = Av.as<float2>();
+          bb.mode = bmode.as<int8_t>(); bb.wf = bwf.as<float>(); bb.wd = bwd.as<double>();
+          bb.lsq = lsq.as<float>(); bb.lcoord = lcoord.as<double>();
+          if (sid) {
+            bb.screens = p->screens.as<float2>();
+            bb.bsid = bsid.as<int32_t>();
+          }
+          WPROJ_TRY(box_fft(p, bb, s));
         }
-        WPROJ_TRY(box_fft(p, bb, s));
         t_fft.stop();
         const dim3 hgrid(ceil_div(per, kSelChunk), nb);
         if (phase == 1) {
@@ -1130,9 +1154,15 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
   if (want_runs) {
     p->m = m;
     p->n_seg = n_seg;
-    WPROJ_TRY(build_runs(p, d_j0.as<int2>(), d_Sk.as<int32_t>(), tile_seg.as<int32_t>(), s));
-    p->fmt = WPROJ_INDEX_TILE_RUNS;
-  } else {
+    const wproj_status st = build_runs(p, d_j0.as<int2>(), d_Sk.as<int32_t>(), tile_seg.as<int32_t>(),
+                                       tptr.as<int64_t>(), &n_rec, s);
+    if (st == WPROJ_OK) {
+      p->fmt = WPROJ_INDEX_TILE_RUNS;
+    } else if (!(st == WPROJ_ERR_UNSUPPORTED && g.index_format == WPROJ_INDEX_AUTO)) {
+      return st;
+    }   // AUTO: rows with more than 64 runs keep the column form
+  }
+  if (p->fmt != WPROJ_INDEX_TILE_RUNS) {
     p->rm_vptr.release();
     p->rm_rptr.release();
     p->rm_org.release();
@@ -1166,19 +1196,21 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
   {
     const bool rec = p->fmt == WPROJ_INDEX_TILE_MASK || p->fmt == WPROJ_INDEX_TILE_RUNS;
     const int64_t chunk = grid_chunk(p->nnz);
+    // the gridding's items in tile order: all segments, or the records of TILE_RUNS
+    const int64_t n_items = p->fmt == WPROJ_INDEX_TILE_RUNS ? n_rec : n_seg;
     DevBuf cntsorted, cum;
-    WPROJ_TRY(cntsorted.alloc(sizeof(int32_t) * std::max<int64_t>(1, n_seg)));
-    WPROJ_TRY(cum.alloc(sizeof(int64_t) * std::max<int64_t>(1, n_seg)));
+    WPROJ_TRY(cntsorted.alloc(sizeof(int32_t) * std::max<int64_t>(1, n_items)));
+    WPROJ_TRY(cum.alloc(sizeof(int64_t) * std::max<int64_t>(1, n_items)));
     if (!rec) WPROJ_TRY(p->seg_meta.alloc(sizeof(SegMeta) * std::max<int64_t>(1, n_seg)));
-    if (n_seg > 0) {
-      k_gather_cnt<<<ceil_div(n_seg, 256), 256, 0, s>>>(n_seg, tile_seg.as<int32_t>(), p->seg_cnt.as<int32_t>(),
+    if (n_items > 0) {
+      k_gather_cnt<<<ceil_div(n_items, 256), 256, 0, s>>>(n_items, tile_seg.as<int32_t>(), p->seg_cnt.as<int32_t>(),
                                                         p->seg_off.as<int64_t>(), p->seg_row.as<int32_t>(),
                                                         cntsorted.as<int32_t>(),
                                                         rec ? nullptr : p->seg_meta.as<SegMeta>());
       WPROJ_CHECK_LAUNCH("gather cnt");
-      WPROJ_TRY(exclusive_scan_i32_to_i64(cntsorted.as<int32_t>(), cum.as<int64_t>(), n_seg, s));
+      WPROJ_TRY(exclusive_scan_i32_to_i64(cntsorted.as<int32_t>(), cum.as<int64_t>(), n_items, s));
     }
-    WPROJ_TRY(make_tile_chunks(n_tiles, tptr.as<int64_t>(), cum.as<int64_t>(), n_seg, p->nnz, chunk, p->chunk_tile,
+    WPROJ_TRY(make_tile_chunks(n_tiles, tptr.as<int64_t>(), cum.as<int64_t>(), n_items, p->nnz, chunk, p->chunk_tile,
                                p->chunk_lo, p->chunk_hi, p->tile_chunk_ptr, &p->n_chunks, s));
     // column format: a cell-major copy for the gridding (packed rows need m <= 2^22)
     p->has_cells = false;

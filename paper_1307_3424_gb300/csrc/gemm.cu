@@ -31,6 +31,13 @@ constexpr int kSliceB = kBN * kBK * 2;
 constexpr int kStages = 2;   // slices in flight (3 CTAs fit on an SM)
 constexpr unsigned long long kGemmWaitNs = 2000000000ull;
 
+// Test hook (wproj_gemm_test_hook): when g_gemm_unset_wait is nonzero every CTA
+// first waits on an mbarrier that nothing ever arrives on, bounded by
+// g_gemm_wait_ns, so the timeout path (error word, drain of the committed MMAs,
+// tensor memory freed) runs without any fault.
+__device__ int g_gemm_unset_wait = 0;
+__device__ unsigned long long g_gemm_wait_ns = kGemmWaitNs;
+
 __device__ __forceinline__ uint32_t su32(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
 
 __device__ __forceinline__ unsigned long long gns() {
@@ -51,12 +58,13 @@ __device__ __forceinline__ bool mbar_test(uint64_t *b, uint32_t parity) {
   return ok != 0;
 }
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *b, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *b, uint32_t parity,
+                                                  unsigned long long limit_ns = kGemmWaitNs) {
   if (mbar_test(b, parity)) return true;
   const unsigned long long t0 = gns();
   for (uint32_t it = 0; it < (1u << 26); ++it) {
     if (mbar_test(b, parity)) return true;
-    if ((it & 63u) == 63u && gns() - t0 > kGemmWaitNs) return false;
+    if ((it & 63u) == 63u && gns() - t0 > limit_ns) return false;
   }
   return false;
 }
@@ -101,6 +109,7 @@ k_gemm_tn(int M, int N, int K, const __nv_bfloat16 *__restrict__ A, const __nv_b
   unsigned char *sa = smem;                              // kStages A slices
   unsigned char *sb = smem + kStages * kSliceA;          // kStages B slices
   __shared__ __align__(8) uint64_t done[kStages];        // MMAs of a stage finished reading it
+  __shared__ __align__(8) uint64_t never;                // test hook: nothing arrives on it
   __shared__ uint32_t tmem_base;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN;
@@ -113,6 +122,7 @@ k_gemm_tn(int M, int N, int K, const __nv_bfloat16 *__restrict__ A, const __nv_b
   if (threadIdx.x == 0) {
     for (int i = 0; i < kStages; ++i)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&done[i])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&never)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -122,6 +132,8 @@ k_gemm_tn(int M, int N, int K, const __nv_bfloat16 *__restrict__ A, const __nv_b
   const uint32_t idesc = instr_desc(kBM, kBN);
   const int nk = K / kBK;
   bool ok = true;
+  if (g_gemm_unset_wait) ok = __syncthreads_and(mbar_wait_bounded(&never, 0, g_gemm_wait_ns));
+  int k_issued = -1;   // last K slice whose MMAs were committed
   // every thread commits one copy group per slice (empty past the end), so
   // slice k's group is complete once at most kStages - 1 younger groups pend
   for (int k = 0; k < kStages; ++k) {
@@ -155,6 +167,7 @@ k_gemm_tn(int M, int N, int K, const __nv_bfloat16 *__restrict__ A, const __nv_b
                        su32(&done[st]))
                    : "memory");
     }
+    k_issued = k;
     // refill this stage with slice k + kStages once its MMAs have read it
     const int nx = k + kStages;
     if (nx < nk) {
@@ -167,10 +180,12 @@ k_gemm_tn(int M, int N, int K, const __nv_bfloat16 *__restrict__ A, const __nv_b
     cp_commit();
   }
   cp_wait<0>();
-  // all MMAs done: the last commit of each stage in use
-  if (ok && nk > 0) {   // the last commit covers every earlier MMA
-    const int kl = nk - 1;
-    ok = __syncthreads_and(mbar_wait_bounded(&done[kl % kStages], (kl / kStages) & 1));
+  // all MMAs done: the last commit covers every earlier MMA.  After a timeout
+  // the committed MMAs are still drained (normal limit) before the tensor
+  // memory is freed.
+  if (k_issued >= 0) {
+    const bool drained = __syncthreads_and(mbar_wait_bounded(&done[k_issued % kStages], (k_issued / kStages) & 1));
+    ok = ok && drained && k_issued == nk - 1;
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (ok) {
@@ -246,6 +261,15 @@ wproj_status gemm_bf16_tn(int M, int N, int K, const __nv_bfloat16 *A, const __n
 
 namespace {
 __device__ int g_gemm_err;   // timeouts of wproj_gemm_bf16 calls
+}
+
+extern "C" wproj_status wproj_gemm_test_hook(int32_t wait_on_unset_barrier, uint64_t limit_ns) {
+  using namespace wproj;
+  const int flag = wait_on_unset_barrier ? 1 : 0;
+  const unsigned long long lim = limit_ns ? (unsigned long long)limit_ns : kGemmWaitNs;
+  WPROJ_CUDA(cudaMemcpyToSymbol(g_gemm_unset_wait, &flag, sizeof(flag)));
+  WPROJ_CUDA(cudaMemcpyToSymbol(g_gemm_wait_ns, &lim, sizeof(lim)));
+  return WPROJ_OK;
 }
 
 extern "C" wproj_status wproj_gemm_bf16(int32_t m, int32_t n, int32_t k, const void *a, const void *b,

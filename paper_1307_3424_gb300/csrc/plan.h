@@ -272,8 +272,10 @@ wproj_status apply_phi_adj(wproj_plan *p, const float2 *y, float *x_re, float2 *
                            const float *z, int mode, cudaStream_t s);
 
 // runs.cu (TILE_RUNS format): both copies from the column form in col / val, which
-// is then released; tile_seg = segments in tile order
-wproj_status build_runs(wproj_plan *p, const int2 *j0, const int32_t *Sk, const int32_t *tile_seg, cudaStream_t s);
+// is then released; tile_seg / tptr = segments in tile order, compacted in place
+// to the n_rec segments that hold entries
+wproj_status build_runs(wproj_plan *p, const int2 *j0, const int32_t *Sk, int32_t *tile_seg, int64_t *tptr,
+                        int64_t *n_rec, cudaStream_t s);
 wproj_status degrid_runs(wproj_plan *p, const float2 *Xt, float2 *y, cudaStream_t s);
 wproj_status grid_runs(wproj_plan *p, const float2 *y, float2 *Xt2, int *launches, cudaStream_t s);
 wproj_status runs_export(const wproj_plan *p, int64_t k0, int64_t k1, int32_t *col_out, void *val_out,

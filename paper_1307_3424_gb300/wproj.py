@@ -30,7 +30,7 @@ EXPORTED = [
     "wproj_dr_state_set", "wproj_phi_noalloc", "wproj_csr_rows",
     "wproj_batch_create", "wproj_batch_destroy", "wproj_batch_build", "wproj_batch_tune",
     "wproj_batch_set_schedule", "wproj_batch_phi", "wproj_batch_phi_adj", "wproj_batch_solve_bpdn",
-    "wproj_batch_get_info", "wproj_gemm_bf16", "wproj_mlp_num_params", "wproj_mlp_create",
+    "wproj_batch_get_info", "wproj_gemm_bf16", "wproj_gemm_test_hook", "wproj_mlp_num_params", "wproj_mlp_create",
     "wproj_mlp_destroy", "wproj_mlp_set_params", "wproj_mlp_get_params", "wproj_mlp_targets",
     "wproj_mlp_forward", "wproj_mlp_gradients", "wproj_mlp_train", "wproj_build_kernels_learned",
     "wproj_daubechies_taps", "wproj_dwt2", "wproj_idwt2", "wproj_set_screens", "wproj_build_kernels_dde",
@@ -146,6 +146,7 @@ def lib() -> ctypes.CDLL:
         "wproj_batch_solve_bpdn": [vp, vp, P(dbl), P(DRParams), vp, vp],
         "wproj_batch_get_info": [vp, P(BatchInfo)],
         "wproj_gemm_bf16": [i32, i32, i32, vp, vp, vp, vp, i32, vp],
+        "wproj_gemm_test_hook": [i32, ctypes.c_uint64],
         "wproj_daubechies_taps": [i32, P(dbl)],
         "wproj_set_screens": [vp, vp, i32, vp],
         "wproj_build_kernels_dde": [vp, vp, i64, vp, dbl, vp],

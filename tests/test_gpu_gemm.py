@@ -50,3 +50,24 @@ def test_gemm_rejects_bad_shapes(wp):
     b = torch.zeros(128, 64, dtype=torch.bfloat16, device="cuda")
     with pytest.raises(wp.WprojError):
         wp.gemm_bf16(a, b)
+
+
+def test_gemm_wait_timeout_is_reported_and_the_context_recovers(wp):
+    # the test hook makes every CTA wait on an mbarrier nothing arrives on, for
+    # 1 ms: the call must report the timeout (no fault, no hang), and the next
+    # call, with the hook off, must give the right product
+    g = torch.Generator().manual_seed(3)
+    a = torch.randn(256, 256, generator=g).to(torch.bfloat16)
+    b = torch.randn(128, 256, generator=g).to(torch.bfloat16)
+    lib = wp.lib()
+    assert lib.wproj_gemm_test_hook(1, 1_000_000) == wp.OK
+    try:
+        with pytest.raises(wp.WprojError) as ei:
+            wp.gemm_bf16(a.cuda(), b.cuda())
+        assert ei.value.status == wp.ERR_TIMEOUT
+        assert b"wait ran out" in lib.wproj_last_error()
+    finally:
+        assert lib.wproj_gemm_test_hook(0, 0) == wp.OK
+    c = wp.gemm_bf16(a.cuda(), b.cuda()).cpu().double()
+    ref = a.double() @ b.double().T
+    assert float((c - ref).norm() / ref.norm()) <= 1e-5

@@ -249,17 +249,18 @@ def test_bf16_and_f16_values(wp):
         check_build(plan, geo, uvw, e, None, tol=tol)
 
 
-@pytest.mark.parametrize("N,M,e,box,vdt", [(32, 200, 1.0, None, "f32"), (64, 150, 0.99, None, "f32"),
-                                           (64, 120, 0.99, None, "bf16"), (128, 60, 0.9, "rule", "f32"),
-                                           (64, 300, 0.99, 32, "f32"), (64, 250, 1.0, 64, "f32"),
-                                           (64, 200, 0.95, 64, "bf16"), (32, 150, 0.9, None, "f16"),
-                                           (128, 400, 0.99, 32, "bf16")])
-def test_index_formats_build_and_operators(wp, N, M, e, box, vdt):
+@pytest.mark.parametrize("N,M,e,box,vdt,wd", [(32, 200, 1.0, None, "f32", 1.0), (64, 150, 0.99, None, "f32", 1.0),
+                                              (64, 120, 0.99, None, "bf16", 1.0), (128, 60, 0.9, "rule", "f32", 1.0),
+                                              (64, 300, 0.99, 32, "f32", 0.05), (64, 250, 1.0, 64, "f32", 1.0),
+                                              (64, 200, 0.95, 64, "bf16", 0.1), (32, 150, 0.9, None, "f16", 0.3),
+                                              (128, 400, 0.99, 32, "bf16", 0.02)])
+def test_index_formats_build_and_operators(wp, N, M, e, box, vdt, wd):
     # the column storages hold the same G (each checked against the oracle) and
     # give the same operators; at e = 1 all match the oracle's operators.  Run
-    # lengths apply when every box is at most 64 x 64 cells.
+    # lengths apply when every box is at most 64 x 64 cells and no row or
+    # segment holds more than 64 runs (w small enough for the box).
     rng = np.random.default_rng(N + M + 1)
-    uvw = synth.random_uvw(rng, M, N, L, 1.0)
+    uvw = synth.random_uvw(rng, M, N, L, wd)
     geo = O.Geometry(N, L)
     x = rng.standard_normal((N, N))
     yv = rng.standard_normal(M) + 1j * rng.standard_normal(M)
