@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--cpu-sample-rows", type=int, default=512,
                     help="rows of the oracle sample timed on the host cores (a few seconds of host work)")
     ap.add_argument("--workload", default="paper",
-                    choices=["paper", "precision", "batched", "learned", "spread", "build"])
+                    choices=["paper", "precision", "batched", "learned", "spread", "build", "gemm"])
     ap.add_argument("--spread-seeds", type=int, default=3, help="spread workload: simulations per point")
     ap.add_argument("--spread-iters", type=int, default=200, help="spread workload: DR iterations")
     ap.add_argument("--train-kernels", type=int, default=2 ** 20, help="learned workload: training kernels")
@@ -678,6 +678,19 @@ def run_learned(args):
     torch.cuda.synchronize()
     t_inf = ev0.elapsed_time(ev1) / 5
     inf_tflops = 65536 * flop_fwd / (t_inf * 1e-3) / 1e12
+    # the GEMM kernel alone on a compute-bound square product (8192^3, FP32 out)
+    gs = 8192
+    ga = torch.randn(gs, gs, device=dev).to(torch.bfloat16)
+    gb = torch.randn(gs, gs, device=dev).to(torch.bfloat16)
+    wproj.gemm_bf16(ga, gb)
+    ev0.record(stream)
+    for _ in range(5):
+        wproj.gemm_bf16(ga, gb)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_sq = ev0.elapsed_time(ev1) / 5
+    sq_tflops = 2.0 * gs ** 3 / (t_sq * 1e-3) / 1e12
+    del ga, gb
     # held-out quality on the training distribution
     offs_h, wc_h = synth.mlp_samples(16384, seed=7)
     uvw_h = torch.from_numpy(synth.mlp_uvw(offs_h, wc_h, wl.N, L, 8)).to(dev)
@@ -717,9 +730,13 @@ def run_learned(args):
                      "fraction_below_1e-2": float(np.mean(eh < 1e-2)), "fraction_below_1e-3": float(np.mean(eh < 1e-3))},
         "training": {"seconds": t_train, "samples_per_s": args.train_steps * batch / t_train,
                      "tflops": train_tflops, "loss_first": losses[0], "loss_last": float(np.mean(losses[-16:]))},
-        "roofline": {"kernel": "k_gemm_tn (MLP forward, 65536 kernels)", "bound": "tensor",
-                     "achieved": inf_tflops, "peak": bf16_peak, "unit": "TFLOP/s", "frac": inf_tflops / bf16_peak,
-                     "traffic": None, "peak_source": "measured (cuBLAS bf16 burst)", "ms": t_inf},
+        "roofline": {"kernel": "k_gemm_ws (8192^3 BF16 product, FP32 out)", "bound": "tensor",
+                     "achieved": sq_tflops, "peak": bf16_peak, "unit": "TFLOP/s", "frac": sq_tflops / bf16_peak,
+                     "traffic": None, "peak_source": "measured (cuBLAS bf16 burst)", "ms": t_sq,
+                     "mlp_forward": {"kernels": 65536, "ms": t_inf, "tflops": inf_tflops,
+                                     "frac": inf_tflops / bf16_peak,
+                                     "output_bytes": 65536 * 3072 * 4,
+                                     "note": "bounded by writing the FP32 output of the last layer"}},
     }
     print(json.dumps(line))
     net.close()
@@ -883,6 +900,47 @@ def run_build(args):
     return 0
 
 
+def run_gemm(args):
+    """The tensor-core GEMM alone (the MLP's contraction): C = A B^T for square
+    BF16 matrices of side --n (default 8192), FP32 out, `steps` timed calls
+    after `warmup`; FLOP rate against the measured BF16 peak."""
+    import torch
+    from paper_1307_3424_gb300 import wproj
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    n = args.n or 8192
+    a = torch.randn(n, n, device=dev).to(torch.bfloat16)
+    b = torch.randn(n, n, device=dev).to(torch.bfloat16)
+    for _ in range(max(1, args.warmup)):
+        wproj.gemm_bf16(a, b)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(0)
+    clocks.start()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        wproj.gemm_bf16(a, b)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    tflops = 2.0 * n ** 3 / (ms * 1e-3) / 1e12
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    pk = float(peaks.get("bf16_tflops", 1900.0))
+    line = {"metric": "gemm_bf16_tflops", "value": tflops, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": f"gemm{n}", "m": n, "n": n, "k": n, "out": "f32"},
+            "roofline": {"kernel": "k_gemm_ws", "bound": "tensor", "achieved": tflops, "peak": pk,
+                         "unit": "TFLOP/s", "frac": tflops / pk, "traffic": None,
+                         "peak_source": "measured (cuBLAS bf16 burst)"},
+            "clocks": clk}
+    print(json.dumps(line))
+    return 0
+
+
 def snr_out_db(x, x_rec):
     """SNR_out = 20 log10(std(x) / std(x - x_rec)) (Section 4.1)."""
     return 20.0 * math.log10(float(np.std(x)) / float(np.std(np.asarray(x) - np.asarray(x_rec))))
@@ -905,6 +963,8 @@ def main():
         return run_spread(args)
     if args.workload == "build":
         return run_build(args)
+    if args.workload == "gemm":
+        return run_gemm(args)
     res = run_ours(args)
     out, kst = res
     if out is not None:

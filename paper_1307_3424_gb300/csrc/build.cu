@@ -314,6 +314,8 @@ k_sel_hist(const float2 *__restrict__ K, int S, SelState *__restrict__ sel,
   const int64_t hi = min(n, lo + kSelChunk);
   const float2 *Kb = K + int64_t(b) * n;
   unsigned lmax = 0;
+  // (grouping lanes by bin with match / reduce before the atomics measured
+  // slower: 389 against 210 ms of selection per paper-scale build)
   for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
     const float a2 = abs2_rn(Kb[i]);
     const unsigned key = __float_as_uint(a2);
