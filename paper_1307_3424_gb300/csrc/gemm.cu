@@ -3,14 +3,15 @@
 // A and B row-major ("K-major"), C row-major FP32 (or BF16).  This is the dense
 // contraction of the learned-kernel MLP (its layers X W^T and their gradients).
 //
-// Persistent and warp-specialised: one CTA per SM walks the 128 x 128 tiles of
-// C (tile t = CTA, CTA + grid, ...; tiles of one row block of A are adjacent, so
-// concurrent CTAs share A rows and B in L2).  Six warps:
+// Persistent and warp-specialised: one CTA per SM walks the 128 x BN tiles of
+// C (BN = 256 when N allows, else 128; tile t = CTA, CTA + grid, ...; tiles of
+// one row block of A are adjacent, so concurrent CTAs share A rows and B in
+// L2).  Six warps:
 //   warp 0   TMA producer: for every 64-wide K slice of a tile, waits for a free
-//            stage, arms its `full` mbarrier with the slice's 32 KB and issues
-//            two cp.async.bulk.tensor loads (A and B boxes of 128 rows x 64
-//            bf16, 128-byte swizzled) that complete on that barrier;
-//   warp 1   MMA issuer: allocates 256 tensor-memory columns (two 128 x 128 FP32
+//            stage, arms its `full` mbarrier with the slice's bytes and issues
+//            two cp.async.bulk.tensor loads (A: 128 rows, B: BN rows, x 64 bf16,
+//            128-byte swizzled) that complete on that barrier;
+//   warp 1   MMA issuer: allocates 2 BN tensor-memory columns (two 128 x BN FP32
 //            accumulators), and for every tile waits for a free accumulator,
 //            issues four tcgen05.mma (kind::f16, K = 16) per slice from
 //            128B-swizzle K-major shared-memory descriptors, commits each slice
@@ -20,7 +21,7 @@
 //            the bias, transpose each 32 x 32 block through shared memory so that
 //            stores are row-contiguous, store, and release the accumulator.
 // So the loads of tile i + 1 and the MMAs of tile i + 1 overlap the epilogue of
-// tile i.  Four stages of 32 KB; 1 CTA per SM.
+// tile i.  Four stages of 48 KB (BN = 256); 1 CTA per SM.
 //
 // Shapes: M, N multiples of 128, K a multiple of 64 (the callers pad).  Every
 // wait is bounded (2 s); a wait that runs out sets *err and its role stops, the
@@ -36,10 +37,9 @@ namespace wproj {
 
 namespace {
 
-constexpr int kBM = 128, kBN = 128, kBK = 64;
-constexpr int kSlice = kBM * kBK * 2;    // bytes of one A (or B) slice: 16 KB
+constexpr int kBM = 128, kBK = 64;      // tile rows; K slice (64 bf16 = one 128-byte swizzle row)
+constexpr int kSliceA = kBM * kBK * 2;   // bytes of one A slice: 16 KB
 constexpr int kStages = 4;
-constexpr int kAccCols = 128;            // tensor-memory columns of one accumulator
 constexpr int kThreads = 192;            // 6 warps
 constexpr unsigned long long kGemmWaitNs = 2000000000ull;
 
@@ -121,22 +121,28 @@ __host__ __device__ constexpr uint32_t instr_desc(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
 }
 
+// BN: tile columns (128 or 256); a tile's accumulator takes BN tensor-memory
+// columns, two of them 2 BN (512 at most: the whole tensor memory).
+template <int BN>
 struct GemmSmem {
-  unsigned char a[kStages][kSlice];      // 1024-byte aligned (swizzle atoms)
-  unsigned char b[kStages][kSlice];
+  unsigned char a[kStages][kSliceA];     // 1024-byte aligned (swizzle atoms)
+  unsigned char b[kStages][BN * kBK * 2];
   float epi[4][32 * 33];                 // epilogue transposes, one block per warp
   uint64_t full[kStages], empty[kStages], acc_full[2], acc_empty[2], never;
   uint32_t tmem_base;
 };
 
-template <bool OUT_BF16>
+template <int BN, bool OUT_BF16>
 __global__ void __launch_bounds__(kThreads, 1)
 k_gemm_ws(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N, int K,
           const float *__restrict__ bias, void *__restrict__ C, int *__restrict__ err) {
+  constexpr int kAccCols = BN;
+  constexpr int kSliceB = BN * kBK * 2;
   extern __shared__ unsigned char smem_raw[];
-  GemmSmem &sm = *reinterpret_cast<GemmSmem *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  GemmSmem<BN> &sm =
+      *reinterpret_cast<GemmSmem<BN> *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nN = N / kBN, n_tiles = (M / kBM) * nN, nk = K / kBK;
+  const int nN = N / BN, n_tiles = (M / kBM) * nN, nk = K / kBK;
   if (threadIdx.x == 0) {
     for (int i = 0; i < kStages; ++i) {
       mbar_init(&sm.full[i], 1);    // the producer's arrive.expect_tx
@@ -169,12 +175,12 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
       uint32_t it = 0;
       for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-        const int m0 = (t / nN) * kBM, n0 = (t % nN) * kBN;
+        const int m0 = (t / nN) * kBM, n0 = (t % nN) * BN;
         for (int k = 0; k < nk; ++k, ++it) {
           const int st = int(it % kStages);
           const uint32_t ph = (it / kStages) & 1u;
           if (!mbar_wait_bounded(&sm.empty[st], ph ^ 1u)) { ok = false; break; }
-          mbar_expect_tx(&sm.full[st], 2 * kSlice);
+          mbar_expect_tx(&sm.full[st], kSliceA + kSliceB);
           tma_load_2d(sm.a[st], &tmA, k * kBK, m0, &sm.full[st]);
           tma_load_2d(sm.b[st], &tmB, k * kBK, n0, &sm.full[st]);
         }
@@ -183,7 +189,7 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   } else if (warp == 1) {
     // ---- MMA issuer (one lane)
     if (lane == 0 && ok) {
-      const uint32_t idesc = instr_desc(kBM, kBN);
+      const uint32_t idesc = instr_desc(kBM, BN);
       uint32_t it = 0, ti = 0;
       for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++ti) {
         const uint32_t buf = ti & 1u, aph = (ti >> 1) & 1u;
@@ -231,12 +237,12 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     float *blk = sm.epi[warp - 2];
     uint32_t ti = 0;
     for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++ti) {
-      const int m0 = (t / nN) * kBM, n0 = (t % nN) * kBN;
+      const int m0 = (t / nN) * kBM, n0 = (t % nN) * BN;
       const uint32_t buf = ti & 1u, aph = (ti >> 1) & 1u;
       if (!mbar_wait_bounded(&sm.acc_full[buf], aph)) { ok = false; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll 1
-      for (int c0 = 0; c0 < kBN; c0 += 32) {
+      for (int c0 = 0; c0 < BN; c0 += 32) {
         uint32_t r[32];
         const uint32_t taddr = tmem + (uint32_t(lg * 32) << 16) + buf * kAccCols + uint32_t(c0);
         asm volatile(
@@ -300,13 +306,13 @@ wproj_status encode_fn(EncodeTiledFn *out) {
   return WPROJ_OK;
 }
 
-// tensor map of a rows x K bf16 row-major matrix, box 128 rows x 64 (128 B), 128-byte swizzle
-wproj_status tensor_map(CUtensorMap *map, const __nv_bfloat16 *p, int rows, int K) {
+// tensor map of a rows x K bf16 row-major matrix, box box_rows x 64 (128 B), 128-byte swizzle
+wproj_status tensor_map(CUtensorMap *map, const __nv_bfloat16 *p, int rows, int K, int box_rows) {
   EncodeTiledFn enc = nullptr;
   WPROJ_TRY(encode_fn(&enc));
   const cuuint64_t dims[2] = {cuuint64_t(K), cuuint64_t(rows)};
   const cuuint64_t strides[1] = {cuuint64_t(K) * 2};
-  const cuuint32_t box[2] = {cuuint32_t(kBK), cuuint32_t(kBM)};
+  const cuuint32_t box[2] = {cuuint32_t(kBK), cuuint32_t(box_rows)};
   const cuuint32_t estr[2] = {1, 1};
   const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(p), dims, strides, box,
                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -315,36 +321,42 @@ wproj_status tensor_map(CUtensorMap *map, const __nv_bfloat16 *p, int rows, int 
   return WPROJ_OK;
 }
 
-}  // namespace
-
-size_t gemm_smem_bytes() { return sizeof(GemmSmem) + 1024; }
-
-// C = A B^T (+ bias); M, N multiples of 128, K a multiple of 64; A and B 16-byte
-// aligned (TMA); err: device int
-wproj_status gemm_bf16_tn(int M, int N, int K, const __nv_bfloat16 *A, const __nv_bfloat16 *B, const float *bias,
-                          void *C, bool out_bf16, int *err, cudaStream_t s) {
-  if (M % kBM || N % kBN || K % kBK || M <= 0 || N <= 0 || K <= 0)
-    return fail(WPROJ_ERR_INVALID_ARG, "gemm: M, N must be multiples of 128 and K of 64");
-  if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15)
-    return fail(WPROJ_ERR_INVALID_ARG, "gemm: A and B must be 16-byte aligned");
+template <int BN>
+wproj_status launch_gemm(int M, int N, int K, const __nv_bfloat16 *A, const __nv_bfloat16 *B, const float *bias,
+                         void *C, bool out_bf16, int *err, cudaStream_t s) {
   CUtensorMap ta, tb;
-  WPROJ_TRY(tensor_map(&ta, A, M, K));
-  WPROJ_TRY(tensor_map(&tb, B, N, K));
+  WPROJ_TRY(tensor_map(&ta, A, M, K, kBM));
+  WPROJ_TRY(tensor_map(&tb, B, N, K, BN));
   int dev = 0, sms = 0;
   WPROJ_CUDA(cudaGetDevice(&dev));
   WPROJ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int n_tiles = (M / kBM) * (N / kBN);
+  const int n_tiles = (M / kBM) * (N / BN);
   const int grid = std::max(1, std::min(n_tiles, sms));
-  const size_t smem = gemm_smem_bytes();
+  const size_t smem = sizeof(GemmSmem<BN>) + 1024;
   if (out_bf16) {
-    WPROJ_CUDA(cudaFuncSetAttribute(k_gemm_ws<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_gemm_ws<true><<<grid, kThreads, smem, s>>>(ta, tb, M, N, K, bias, C, err);
+    WPROJ_CUDA(cudaFuncSetAttribute(k_gemm_ws<BN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_gemm_ws<BN, true><<<grid, kThreads, smem, s>>>(ta, tb, M, N, K, bias, C, err);
   } else {
-    WPROJ_CUDA(cudaFuncSetAttribute(k_gemm_ws<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_gemm_ws<false><<<grid, kThreads, smem, s>>>(ta, tb, M, N, K, bias, C, err);
+    WPROJ_CUDA(cudaFuncSetAttribute(k_gemm_ws<BN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_gemm_ws<BN, false><<<grid, kThreads, smem, s>>>(ta, tb, M, N, K, bias, C, err);
   }
   WPROJ_CHECK_LAUNCH("gemm");
   return WPROJ_OK;
+}
+
+}  // namespace
+
+// C = A B^T (+ bias); M, N multiples of 128, K a multiple of 64; A and B 16-byte
+// aligned (TMA); err: device int.  Tiles of 128 x 256 when N is a multiple of
+// 256, else 128 x 128.
+wproj_status gemm_bf16_tn(int M, int N, int K, const __nv_bfloat16 *A, const __nv_bfloat16 *B, const float *bias,
+                          void *C, bool out_bf16, int *err, cudaStream_t s) {
+  if (M % kBM || N % 128 || K % kBK || M <= 0 || N <= 0 || K <= 0)
+    return fail(WPROJ_ERR_INVALID_ARG, "gemm: M, N must be multiples of 128 and K of 64");
+  if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15)
+    return fail(WPROJ_ERR_INVALID_ARG, "gemm: A and B must be 16-byte aligned");
+  if (N % 256 == 0) return launch_gemm<256>(M, N, K, A, B, bias, C, out_bf16, err, s);
+  return launch_gemm<128>(M, N, K, A, B, bias, C, out_bf16, err, s);
 }
 
 }  // namespace wproj
