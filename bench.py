@@ -608,7 +608,8 @@ def run_batched(args):
                    "M_total": info["m"], "pixels_total": info["pixels"], "nnz": info["nnz"], "e": bw.e,
                    "w_c_max": f"U[0, {bw.wc_max}] per problem", "box": "rule S(w)", "dr_inner_iters": INNER,
                    "pairs_per_step": PAIRS_PER_STEP, "index_format": "columns",
-                   "schedule": {"piece": sched["piece"], "chunk": sched["chunk"]},
+                   "schedule": {"piece": sched["piece"], "chunk": sched["chunk"],
+                                "lanes_per_piece": sched["lanes_per_piece"]},
                    "l2": "inputs larger than L2 (G exceeds L2 many times)", "parallelism": "one GPU"},
         "problem_pairs_per_s": value * len(ns),
         "e2e": {"value": PAIRS_PER_STEP * args.steps / (t_e2e * 1e-3), "unit": "batch pairs/s",

@@ -447,12 +447,15 @@ wproj_status wproj_build_kernels_learned(wproj_plan *p, wproj_mlp *n, const doub
 typedef struct wproj_batch wproj_batch;
 
 /* Work split of the batch operators: degridding row pieces of <= piece entries,
+ * each taken by lanes_per_piece lanes of a warp (32, 16, 8 or 4: 32 / lanes pieces
+ * per warp),
  * gridding chunks of about chunk entries of one grid tile. */
 typedef struct {
   int64_t piece;
   int64_t chunk;
   double degrid_ms;     /* wproj_batch_tune: measured time of the chosen schedules */
   double grid_ms;
+  int32_t lanes_per_piece;
 } wproj_batch_schedule;
 
 typedef struct {
@@ -463,6 +466,7 @@ typedef struct {
   int64_t n_pieces, n_chunks, piece, chunk;
   int64_t launches;     /* kernels launched by batch operator and solver calls */
   int64_t iter_launches;  /* kernels in one captured Douglas-Rachford iteration */
+  int32_t lanes_per_piece;  /* degridding lanes per row piece (32, 16, 8 or 4) */
 } wproj_batch_info;
 
 /* n problems (1 <= n <= 65535) with geometries descs[n] (host); each is validated
@@ -475,12 +479,14 @@ wproj_status wproj_batch_destroy(wproj_batch *b);
  * Sets a default schedule (piece 1024, chunk 8192). */
 wproj_status wproj_batch_build(wproj_batch *b, const double *uvw, const int64_t *m, double e, void *stream);
 
-/* Times candidate schedules on this batch (pieces 256 .. 16384 entries, chunks
- * 2048 .. 65536 entries), keeps the fastest of each; out (host) may be NULL.
- * Synchronous. */
+/* Times candidate schedules on this batch (pieces 64 .. 16384 entries taken by
+ * 32, 16, 8 or 4 lanes, chunks 2048 .. 65536 entries), keeps the fastest of each; out
+ * (host) may be NULL.  Synchronous. */
 wproj_status wproj_batch_tune(wproj_batch *b, wproj_batch_schedule *out, void *stream);
-/* Sets a schedule explicitly (piece, chunk >= 32).  Synchronous. */
-wproj_status wproj_batch_set_schedule(wproj_batch *b, int64_t piece, int64_t chunk, void *stream);
+/* Sets a schedule explicitly (piece, chunk >= 32; lanes_per_piece 32, 16, 8 or 4, 0
+ * keeps the current one; anything else is WPROJ_ERR_INVALID_ARG).  Synchronous. */
+wproj_status wproj_batch_set_schedule(wproj_batch *b, int64_t piece, int64_t chunk, int32_t lanes_per_piece,
+                                      void *stream);
 
 /* y = Phi x and x_re = Re Phi^H y for every problem (layouts above). */
 wproj_status wproj_batch_phi(wproj_batch *b, const float *x, void *y, void *stream);

@@ -43,6 +43,7 @@ struct wproj_batch {
   wproj::DevBuf tile_ent, cell_ent, cell_val;
   // schedule
   int64_t piece = 0, chunk = 0, n_pieces = 0, n_chunks = 0;
+  int lpp = 32;   // degridding lanes per row piece (32, 16, 8 or 4: the row-split schedule)
   wproj::DevBuf piece_row, piece_lo, piece_len, row_piece_ptr;
   wproj::DevBuf chunk_tile, chunk_lo, chunk_hi, chunk_prob, tile_chunk_ptr;
   wproj::DevBuf piece_partial, grid_partial;
@@ -239,6 +240,7 @@ BatchOps ops_of(const wproj_batch *b) {
   o.m = b->m;
   o.n_pieces = b->n_pieces;
   o.n_chunks = b->n_chunks;
+  o.lpp = b->lpp;
   o.n_tiles = b->tiles;
   o.col = b->col.as<int32_t>();
   o.val = b->val.ptr;
@@ -291,6 +293,10 @@ wproj_status set_pieces(wproj_batch *b, int64_t piece, cudaStream_t s) {
                             b->row_piece_ptr, &b->n_pieces, s));
   WPROJ_TRY(b->piece_partial.alloc(sizeof(float2) * std::max<int64_t>(1, b->n_pieces)));
   b->piece = piece;
+  if (b->dr_exec) {   // the captured iteration holds the old buffers
+    cudaGraphExecDestroy(b->dr_exec);
+    b->dr_exec = nullptr;
+  }
   return WPROJ_OK;
 }
 
@@ -573,20 +579,27 @@ wproj_status batch_build_impl(wproj_batch *b, const double *uvw, const int64_t *
 }
 
 wproj_status batch_tune_impl(wproj_batch *b, wproj_batch_schedule *out, cudaStream_t s) {
-  static const int64_t pieces[] = {256, 512, 1024, 2048, 4096, 16384};
+  static const int64_t pieces[] = {64, 256, 512, 1024, 2048, 4096, 16384};
+  static const int lanes[] = {32, 16, 8, 4};
   static const int64_t chunks[] = {2048, 4096, 8192, 16384, 65536};
   double best = 1e30;
   int64_t bp = b->piece;
+  int bl = b->lpp;
   WPROJ_CUDA(cudaMemsetAsync(b->Xt.ptr, 0, sizeof(float2) * b->grid, s));
   WPROJ_CUDA(cudaMemsetAsync(b->u.ptr, 0, sizeof(float2) * b->m, s));
+  // row split: pieces of at most `piece` entries, each taken by 32, 16, 8 or 4 lanes
   for (int64_t pc : pieces) {
     WPROJ_TRY(set_pieces(b, pc, s));
-    double ms = 0;
-    WPROJ_TRY(time_ms([&] { return batch_degrid(ops_of(b), b->Xt.as<float2>(), b->piece_partial.as<float2>(),
-                                                b->r.as<float2>(), s); }, 5, s, &ms));
-    if (ms < best) { best = ms; bp = pc; }
+    for (int l : lanes) {
+      b->lpp = l;
+      double ms = 0;
+      WPROJ_TRY(time_ms([&] { return batch_degrid(ops_of(b), b->Xt.as<float2>(), b->piece_partial.as<float2>(),
+                                                  b->r.as<float2>(), s); }, 5, s, &ms));
+      if (ms < best) { best = ms; bp = pc; bl = l; }
+    }
   }
   const double deg_ms = best;
+  b->lpp = bl;
   WPROJ_TRY(set_pieces(b, bp, s));
   best = 1e30;
   int64_t bc = b->chunk;
@@ -600,6 +613,7 @@ wproj_status batch_tune_impl(wproj_batch *b, wproj_batch_schedule *out, cudaStre
   WPROJ_TRY(set_chunks(b, bc, s));
   if (out) {
     out->piece = bp;
+    out->lanes_per_piece = bl;
     out->chunk = bc;
     out->degrid_ms = deg_ms;
     out->grid_ms = best;
@@ -731,9 +745,14 @@ wproj_status wproj_batch_tune(wproj_batch *b, wproj_batch_schedule *out, void *s
   return batch_tune_impl(b, out, as_stream(stream));
 }
 
-wproj_status wproj_batch_set_schedule(wproj_batch *b, int64_t piece, int64_t chunk, void *stream) {
+wproj_status wproj_batch_set_schedule(wproj_batch *b, int64_t piece, int64_t chunk, int32_t lanes_per_piece,
+                                      void *stream) {
   if (!b || !b->built) return fail(WPROJ_ERR_NOT_BUILT, "batch_set_schedule: build the batch first");
   if (piece < 32 || chunk < 32) return fail(WPROJ_ERR_INVALID_ARG, "batch_set_schedule: piece and chunk >= 32");
+  if (lanes_per_piece != 0 && lanes_per_piece != 4 && lanes_per_piece != 8 && lanes_per_piece != 16 &&
+      lanes_per_piece != 32)
+    return fail(WPROJ_ERR_INVALID_ARG, "batch_set_schedule: lanes_per_piece is 32, 16, 8 or 4");
+  if (lanes_per_piece) b->lpp = lanes_per_piece;
   WPROJ_TRY(set_pieces(b, piece, as_stream(stream)));
   return set_chunks(b, chunk, as_stream(stream));
 }
@@ -779,6 +798,7 @@ wproj_status wproj_batch_get_info(const wproj_batch *b, wproj_batch_info *out) {
   out->n_chunks = b->n_chunks;
   out->piece = b->piece;
   out->chunk = b->chunk;
+  out->lanes_per_piece = b->lpp;
   out->launches = b->launches;
   out->iter_launches = b->iter_launches;
   return WPROJ_OK;

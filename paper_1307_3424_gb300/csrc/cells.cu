@@ -27,6 +27,7 @@ namespace {
 
 constexpr int kCellWarps = 8;
 constexpr unsigned kCellMask = 1023u;
+constexpr int kAheadE = 2, kAheadY = 1;   // gridding load pipeline depths (windows of 32 entries; deeper measured slower)
 
 // exclusive scan of v over a block of 1024 threads; returns the thread's prefix
 __device__ __forceinline__ int block_excl_scan_1024(int v, int *wsum) {
@@ -155,19 +156,36 @@ k_grid_cells(const int64_t *__restrict__ tile_ent, const uint32_t *__restrict__ 
   int carry_cell = -1;          // run left open by the previous window
   float2 carry = make_float2(0.f, 0.f);
   bool head_done = false;       // the warp's first run has been closed
-  // software pipeline: entries and values two windows ahead, y one window ahead
+  // software pipeline: entries and values kAheadE windows ahead, y kAheadY
+  // windows ahead (a window's y needs its entries, loaded kAheadE - kAheadY
+  // windows earlier), so that several windows' loads are in flight per warp
   auto load_e = [&](int64_t ws) { return ws + lane < b ? __ldg(cell_ent + ws + lane) : 0u; };
   auto load_v = [&](int64_t ws) {
     return ws + lane < b ? cell_value<VDT>(cell_val, ws + lane) : make_float2(0.f, 0.f);
   };
   auto load_y = [&](int64_t ws, uint32_t e) { return ws + lane < b ? __ldg(y + (e >> 10)) : make_float2(0.f, 0.f); };
-  uint32_t e_cur = load_e(a), e_nxt = load_e(a + 32);
-  float2 v_cur = load_v(a), v_nxt = load_v(a + 32);
-  float2 y_cur = load_y(a, e_cur);
+  uint32_t eq[kAheadE];
+  float2 vq[kAheadE], yq[kAheadY];
+#pragma unroll
+  for (int k = 0; k < kAheadE; ++k) {
+    eq[k] = load_e(a + 32 * k);
+    vq[k] = load_v(a + 32 * k);
+  }
+#pragma unroll
+  for (int k = 0; k < kAheadY; ++k) yq[k] = load_y(a + 32 * k, eq[k]);
   for (int64_t ws = a; ws < b; ws += 32) {
-    const uint32_t e_far = load_e(ws + 64);
-    const float2 v_far = load_v(ws + 64);
-    const float2 y_nxt = load_y(ws + 32, e_nxt);
+    const uint32_t e_cur = eq[0];
+    const float2 v_cur = vq[0], y_cur = yq[0];
+#pragma unroll
+    for (int k = 0; k + 1 < kAheadE; ++k) {
+      eq[k] = eq[k + 1];
+      vq[k] = vq[k + 1];
+    }
+#pragma unroll
+    for (int k = 0; k + 1 < kAheadY; ++k) yq[k] = yq[k + 1];
+    eq[kAheadE - 1] = load_e(ws + 32 * kAheadE);
+    vq[kAheadE - 1] = load_v(ws + 32 * kAheadE);
+    yq[kAheadY - 1] = load_y(ws + 32 * kAheadY, eq[kAheadY - 1]);
     const int last_valid = int(b - ws < 32 ? b - ws : 32) - 1;
     const bool valid = lane <= last_valid;
     int cell = 2048 + lane;     // invalid lanes form runs of their own
@@ -176,11 +194,6 @@ k_grid_cells(const int64_t *__restrict__ tile_ent, const uint32_t *__restrict__ 
       cell = int(e_cur & kCellMask);
       t = make_float2(v_cur.x * y_cur.x + v_cur.y * y_cur.y, v_cur.x * y_cur.y - v_cur.y * y_cur.x);   // conj(v) y
     }
-    e_cur = e_nxt;
-    e_nxt = e_far;
-    v_cur = v_nxt;
-    v_nxt = v_far;
-    y_cur = y_nxt;
     if (carry_cell >= 0 && __shfl_sync(0xffffffffu, cell, 0) != carry_cell) {
       // the carried run ended exactly at the window boundary
       if (!head_done) {

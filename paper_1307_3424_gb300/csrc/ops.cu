@@ -29,46 +29,77 @@ __device__ __forceinline__ float2 load_val(const void *__restrict__ val, int64_t
   }
 }
 
-template <int VDT>
-__global__ void __launch_bounds__(256)
-k_degrid(int64_t n_pieces, const int32_t *__restrict__ piece_lo_row, const int64_t *__restrict__ piece_lo,
-         const int32_t *__restrict__ piece_len, const int32_t *__restrict__ col,
-         const void *__restrict__ val, const float2 *__restrict__ Xt, float2 *__restrict__ partial) {
-  const int lane = threadIdx.x & 31;
+constexpr int kDegridBlocksPerSm = 6;   // 40 registers a thread: six resident 256-thread blocks
+
+// LPP lanes per row piece (32, 16, 8 or 4): 32 / LPP pieces per warp step, so
+// that short pieces still put several independent loads in flight per lane.
+// Each lane takes up to four entries per step (predicated, all issued before
+// the first use), and the next step's piece header is loaded one step ahead,
+// leaving the column -> grid-value chain as the only dependent loads.
+template <int VDT, int LPP>
+__global__ void __launch_bounds__(256, kDegridBlocksPerSm)
+k_degrid(int64_t n_pieces, const int64_t *__restrict__ piece_lo, const int32_t *__restrict__ piece_len,
+         const int32_t *__restrict__ col, const void *__restrict__ val, const float2 *__restrict__ Xt,
+         float2 *__restrict__ partial) {
+  constexpr int kPer = 32 / LPP;   // pieces per warp step
+  const int lane = threadIdx.x & 31, sl = lane % LPP;
   const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  for (int64_t pc = warp; pc < n_pieces; pc += nwarps) {
-    const int64_t lo = piece_lo[pc];
-    const int len = piece_len[pc];
+  const int64_t stride = ((int64_t(gridDim.x) * blockDim.x) >> 5) * kPer;
+  int64_t pc = warp * kPer + lane / LPP;
+  int64_t lo = pc < n_pieces ? piece_lo[pc] : 0;
+  int len = pc < n_pieces ? piece_len[pc] : 0;
+  for (int64_t base = warp * kPer; base < n_pieces; base += stride, pc += stride) {
+    const int64_t npc = pc + stride;
+    const int64_t nlo = npc < n_pieces ? piece_lo[npc] : 0;
+    const int nlen = npc < n_pieces ? piece_len[npc] : 0;
     float ax = 0.f, ay = 0.f, bx = 0.f, by = 0.f;
-    int i = lane;
-    for (; i + 96 < len; i += 128) {
-      const int c0 = __ldg(col + lo + i), c1 = __ldg(col + lo + i + 32);
-      const int c2 = __ldg(col + lo + i + 64), c3 = __ldg(col + lo + i + 96);
-      const float2 v0 = load_val<VDT>(val, lo + i), v1 = load_val<VDT>(val, lo + i + 32);
-      const float2 v2 = load_val<VDT>(val, lo + i + 64), v3 = load_val<VDT>(val, lo + i + 96);
-      const float2 x0 = __ldg(Xt + c0), x1 = __ldg(Xt + c1), x2 = __ldg(Xt + c2), x3 = __ldg(Xt + c3);
-      ax = fmaf(v0.x, x0.x, ax); ax = fmaf(-v0.y, x0.y, ax); ay = fmaf(v0.x, x0.y, ay); ay = fmaf(v0.y, x0.x, ay);
-      bx = fmaf(v1.x, x1.x, bx); bx = fmaf(-v1.y, x1.y, bx); by = fmaf(v1.x, x1.y, by); by = fmaf(v1.y, x1.x, by);
-      ax = fmaf(v2.x, x2.x, ax); ax = fmaf(-v2.y, x2.y, ax); ay = fmaf(v2.x, x2.y, ay); ay = fmaf(v2.y, x2.x, ay);
-      bx = fmaf(v3.x, x3.x, bx); bx = fmaf(-v3.y, x3.y, bx); by = fmaf(v3.x, x3.y, by); by = fmaf(v3.y, x3.x, by);
-    }
-    for (; i < len; i += 32) {
-      const int c0 = __ldg(col + lo + i);
-      const float2 v0 = load_val<VDT>(val, lo + i);
-      const float2 x0 = __ldg(Xt + c0);
-      ax = fmaf(v0.x, x0.x, ax); ax = fmaf(-v0.y, x0.y, ax); ay = fmaf(v0.x, x0.y, ay); ay = fmaf(v0.y, x0.x, ay);
+    for (int i = sl; i < len; i += 4 * LPP) {
+      int c[4];
+      float2 v[4], x[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const bool ok = i + k * LPP < len;
+        c[k] = ok ? __ldg(col + lo + i + k * LPP) : 0;
+        v[k] = ok ? load_val<VDT>(val, lo + i + k * LPP) : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) x[k] = i + k * LPP < len ? __ldg(Xt + c[k]) : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < 4; k += 2) {
+        ax = fmaf(v[k].x, x[k].x, ax); ax = fmaf(-v[k].y, x[k].y, ax);
+        ay = fmaf(v[k].x, x[k].y, ay); ay = fmaf(v[k].y, x[k].x, ay);
+        bx = fmaf(v[k + 1].x, x[k + 1].x, bx); bx = fmaf(-v[k + 1].y, x[k + 1].y, bx);
+        by = fmaf(v[k + 1].x, x[k + 1].y, by); by = fmaf(v[k + 1].y, x[k + 1].x, by);
+      }
     }
     ax += bx;
     ay += by;
 #pragma unroll
-    for (int o = 16; o; o >>= 1) {
+    for (int o = LPP / 2; o; o >>= 1) {   // within the piece's lanes
       ax += __shfl_xor_sync(0xffffffffu, ax, o);
       ay += __shfl_xor_sync(0xffffffffu, ay, o);
     }
-    if (lane == 0) partial[pc] = make_float2(ax, ay);
+    if (pc < n_pieces && sl == 0) partial[pc] = make_float2(ax, ay);
+    lo = nlo;
+    len = nlen;
   }
-  (void)piece_lo_row;
+}
+
+template <int VDT>
+wproj_status launch_degrid_pieces(int64_t n_pieces, const int64_t *piece_lo, const int32_t *piece_len,
+                                  const int32_t *col, const void *val, const float2 *Xt, float2 *partial, int lpp,
+                                  cudaStream_t s) {
+  const int64_t warps = ceil_div(n_pieces, int64_t(32 / lpp));
+  // one resident wave: every block strides over the same share of pieces
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(warps * 32, 256), 152 * kDegridBlocksPerSm));
+  switch (lpp) {
+    case 4: k_degrid<VDT, 4><<<blocks, 256, 0, s>>>(n_pieces, piece_lo, piece_len, col, val, Xt, partial); break;
+    case 8: k_degrid<VDT, 8><<<blocks, 256, 0, s>>>(n_pieces, piece_lo, piece_len, col, val, Xt, partial); break;
+    case 16: k_degrid<VDT, 16><<<blocks, 256, 0, s>>>(n_pieces, piece_lo, piece_len, col, val, Xt, partial); break;
+    default: k_degrid<VDT, 32><<<blocks, 256, 0, s>>>(n_pieces, piece_lo, piece_len, col, val, Xt, partial);
+  }
+  WPROJ_CHECK_LAUNCH("degrid");
+  return WPROJ_OK;
 }
 
 __global__ void k_degrid_reduce(int64_t m, const int32_t *__restrict__ row_piece_ptr,
@@ -186,19 +217,21 @@ __global__ void k_grid_reduce(const int32_t *__restrict__ tile_chunk_ptr, const 
 constexpr int kGridWarps = 8;
 
 // Column-format degridding kernels; partial sums per row piece into `partial`.
+// A piece takes the fewest lanes whose four-entry steps cover its average length.
 wproj_status launch_degrid_cols(wproj_plan *p, const float2 *Xt, float2 *partial, cudaStream_t s) {
-  const int blocks = (int)std::min<int64_t>(ceil_div(p->n_pieces * 32, 256), 152 * 16);
-#define DEGRID_COLS(VDT)                                                                                     \
-  k_degrid<VDT><<<blocks, 256, 0, s>>>(p->n_pieces, p->piece_row.as<int32_t>(), p->piece_lo.as<int64_t>(),  \
-                                       p->piece_len.as<int32_t>(), p->col.as<int32_t>(), p->val.ptr, Xt, partial)
+  int lpp = 4;
+  while (lpp < 32 && 4 * lpp * p->n_pieces < p->nnz) lpp *= 2;
   switch (p->g.value_dtype) {
-    case WPROJ_VAL_F32: DEGRID_COLS(WPROJ_VAL_F32); break;
-    case WPROJ_VAL_BF16: DEGRID_COLS(WPROJ_VAL_BF16); break;
-    default: DEGRID_COLS(WPROJ_VAL_F16);
+    case WPROJ_VAL_F32:
+      return launch_degrid_pieces<WPROJ_VAL_F32>(p->n_pieces, p->piece_lo.as<int64_t>(), p->piece_len.as<int32_t>(),
+                                                 p->col.as<int32_t>(), p->val.ptr, Xt, partial, lpp, s);
+    case WPROJ_VAL_BF16:
+      return launch_degrid_pieces<WPROJ_VAL_BF16>(p->n_pieces, p->piece_lo.as<int64_t>(), p->piece_len.as<int32_t>(),
+                                                  p->col.as<int32_t>(), p->val.ptr, Xt, partial, lpp, s);
+    default:
+      return launch_degrid_pieces<WPROJ_VAL_F16>(p->n_pieces, p->piece_lo.as<int64_t>(), p->piece_len.as<int32_t>(),
+                                                 p->col.as<int32_t>(), p->val.ptr, Xt, partial, lpp, s);
   }
-#undef DEGRID_COLS
-  WPROJ_CHECK_LAUNCH("degrid");
-  return WPROJ_OK;
 }
 
 }  // namespace
@@ -299,10 +332,8 @@ wproj_status csr_rows(const wproj_plan *p, int64_t k0, int64_t k1, int32_t *col_
 // ---- batches: the column-format kernels over a batch's concatenated arrays ------
 
 wproj_status batch_degrid(const BatchOps &b, const float2 *Xt, float2 *partial, float2 *y, cudaStream_t s) {
-  const int blocks = (int)std::min<int64_t>(ceil_div(b.n_pieces * 32, 256), 152 * 16);
-  k_degrid<WPROJ_VAL_F32><<<std::max(blocks, 1), 256, 0, s>>>(b.n_pieces, b.piece_row, b.piece_lo, b.piece_len,
-                                                              b.col, b.val, Xt, partial);
-  WPROJ_CHECK_LAUNCH("batch degrid");
+  WPROJ_TRY(launch_degrid_pieces<WPROJ_VAL_F32>(b.n_pieces, b.piece_lo, b.piece_len, b.col, b.val, Xt, partial,
+                                                b.lpp, s));
   k_degrid_reduce<<<ceil_div(b.m, 256), 256, 0, s>>>(b.m, b.row_piece_ptr, partial, nullptr, y);
   WPROJ_CHECK_LAUNCH("batch degrid reduce");
   return WPROJ_OK;

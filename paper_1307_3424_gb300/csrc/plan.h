@@ -56,6 +56,7 @@ struct BProb {
 // The column-format operator arrays of a batch (concatenated over problems).
 struct BatchOps {
   int64_t m = 0, n_pieces = 0, n_chunks = 0, n_tiles = 0;
+  int lpp = 32;                          // degridding lanes per row piece (32, 16, 8 or 4)
   const int32_t *col = nullptr;          // columns + the problem's grid_off
   const void *val = nullptr;             // complex64
   const int32_t *piece_row = nullptr, *piece_len = nullptr, *row_piece_ptr = nullptr;

@@ -72,14 +72,14 @@ class SolveInfo(ctypes.Structure):
 
 class BatchSchedule(ctypes.Structure):
     _fields_ = [("piece", ctypes.c_int64), ("chunk", ctypes.c_int64), ("degrid_ms", ctypes.c_double),
-                ("grid_ms", ctypes.c_double)]
+                ("grid_ms", ctypes.c_double), ("lanes_per_piece", ctypes.c_int32)]
 
 
 class BatchInfo(ctypes.Structure):
     _fields_ = [("n_problems", ctypes.c_int32), ("m", ctypes.c_int64), ("pixels", ctypes.c_int64),
                 ("nnz", ctypes.c_int64), ("n_pieces", ctypes.c_int64), ("n_chunks", ctypes.c_int64),
                 ("piece", ctypes.c_int64), ("chunk", ctypes.c_int64), ("launches", ctypes.c_int64),
-                ("iter_launches", ctypes.c_int64)]
+                ("iter_launches", ctypes.c_int64), ("lanes_per_piece", ctypes.c_int32)]
 
 
 class LearnedInfo(ctypes.Structure):
@@ -140,7 +140,7 @@ def lib() -> ctypes.CDLL:
         "wproj_batch_destroy": [vp],
         "wproj_batch_build": [vp, vp, P(i64), dbl, vp],
         "wproj_batch_tune": [vp, P(BatchSchedule), vp],
-        "wproj_batch_set_schedule": [vp, i64, i64, vp],
+        "wproj_batch_set_schedule": [vp, i64, i64, ctypes.c_int32, vp],
         "wproj_batch_phi": [vp, vp, vp, vp],
         "wproj_batch_phi_adj": [vp, vp, vp, vp],
         "wproj_batch_solve_bpdn": [vp, vp, P(dbl), P(DRParams), vp, vp],
@@ -541,8 +541,9 @@ class Batch:
         _check(lib().wproj_batch_tune(self._h, ctypes.byref(out), _stream(stream)))
         return {f: getattr(out, f) for f, _ in out._fields_}
 
-    def set_schedule(self, piece: int, chunk: int, stream=None):
-        _check(lib().wproj_batch_set_schedule(self._h, int(piece), int(chunk), _stream(stream)))
+    def set_schedule(self, piece: int, chunk: int, lanes_per_piece: int = 0, stream=None):
+        _check(lib().wproj_batch_set_schedule(self._h, int(piece), int(chunk), int(lanes_per_piece),
+                                              _stream(stream)))
 
     def info(self) -> dict:
         out = BatchInfo()

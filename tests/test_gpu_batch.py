@@ -110,12 +110,17 @@ def test_batch_adjoint_identity_and_schedules(wp):
         lhs = np.real(np.vdot(bb.numpy().astype(np.complex128), a.numpy().astype(np.complex128)))
         rhs = float(np.dot(c.numpy().ravel().astype(np.float64), d.numpy().ravel().astype(np.float64)))
         assert abs(lhs - rhs) <= 1e-5 * max(1.0, abs(lhs))
-    for piece, chunk in ((32, 32), (300, 5000), (16384, 65536)):
-        b.set_schedule(piece, chunk)
+    for piece, chunk, lanes in ((32, 32, 8), (300, 5000, 32), (64, 2048, 4), (16384, 65536, 16),
+                                (16384, 65536, 4)):
+        b.set_schedule(piece, chunk, lanes)
+        assert b.info()["lanes_per_piece"] == lanes
         assert rel(b.phi(x).cpu().numpy(), ref_y) <= 1e-6
         assert rel(b.phi_adj(y).cpu().numpy(), ref_x) <= 1e-6
+    with pytest.raises(wp.WprojError):
+        b.set_schedule(256, 256, 12)
     sch = b.tune()
     assert sch["piece"] >= 32 and sch["chunk"] >= 32 and sch["degrid_ms"] > 0 and sch["grid_ms"] > 0
+    assert sch["lanes_per_piece"] in (4, 8, 16, 32) and b.info()["lanes_per_piece"] == sch["lanes_per_piece"]
     assert rel(b.phi(x).cpu().numpy(), ref_y) <= 1e-6
     b.close()
 
