@@ -40,6 +40,25 @@ __device__ __forceinline__ int img_to_pad(int p, int N, int G) {
   return (p >= h) ? p - h : p - h + G;
 }
 
+// Block copy of TOT elements into shared memory, element idx from ld(idx) and
+// stored by st(idx, v): all of a thread's loads are issued before its first
+// store, so a thread keeps TOT / T loads in flight instead of one.
+template <int TOT, int T, class LD, class ST>
+__device__ __forceinline__ void staged_copy(LD ld, ST st) {
+  constexpr int PER = (TOT + T - 1) / T;
+  float2 r[PER];
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int idx = int(threadIdx.x) + i * T;
+    r[i] = (TOT % T == 0 || idx < TOT) ? ld(idx) : make_float2(0.f, 0.f);
+  }
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int idx = int(threadIdx.x) + i * T;
+    if (TOT % T == 0 || idx < TOT) st(idx, r[i]);
+  }
+}
+
 // ---- Phi: F Z A --------------------------------------------------------------
 
 // Each pass is a device body (block `blk` of one transform set) called by a
@@ -54,20 +73,22 @@ __device__ __forceinline__ void phi_fwd_rows_body(const float *__restrict__ x, c
   constexpr int G = 1 << LOGN;
   extern __shared__ float2 sm[];
   const int p0 = blk * Cfg::C;
-  for (int idx = threadIdx.x; idx < Cfg::C * G; idx += Cfg::T) {
-    const int c = idx / G, Q = idx % G;
-    const int p = p0 + c;
-    float2 v = make_float2(0.f, 0.f);
-    if (p < N) {
-      const int q = pad_to_img(Q, N, G);
-      if (q >= 0) {
-        const float s = inv_a[p] * inv_a[q];
-        if (xc) v = cscale(xc[int64_t(p) * N + q], s);
-        else v = make_float2(x[int64_t(p) * N + q] * s, 0.f);
-      }
-    }
-    sm[c * Cfg::LD + Q] = v;
-  }
+  staged_copy<Cfg::C * G, Cfg::T>(
+      [&](int idx) {
+        const int c = idx / G, Q = idx % G;
+        const int p = p0 + c;
+        float2 v = make_float2(0.f, 0.f);
+        if (p < N) {
+          const int q = pad_to_img(Q, N, G);
+          if (q >= 0) {
+            const float s = inv_a[p] * inv_a[q];
+            if (xc) v = cscale(xc[int64_t(p) * N + q], s);
+            else v = make_float2(x[int64_t(p) * N + q] * s, 0.f);
+          }
+        }
+        return v;
+      },
+      [&](int idx, float2 v) { sm[(idx / G) * Cfg::LD + idx % G] = v; });
   __syncthreads();
   fft_block<LOGN, Cfg::C, Cfg::T, -1>(sm, Cfg::LD, tw);
   for (int idx = threadIdx.x; idx < Cfg::C * G; idx += Cfg::T) {
@@ -99,13 +120,13 @@ __device__ __forceinline__ void phi_fwd_cols_body(const float2 *__restrict__ int
   constexpr int G = 1 << LOGN;
   extern __shared__ float2 sm[];
   const int Q0 = blk * Cfg::C;
-  for (int idx = threadIdx.x; idx < Cfg::C * G; idx += Cfg::T) {
-    const int P = idx / Cfg::C, c = idx % Cfg::C;
-    const int p = pad_to_img(P, N, G);
-    float2 v = make_float2(0.f, 0.f);
-    if (p >= 0 && Q0 + c < G) v = inter[int64_t(p) * G + Q0 + c];
-    sm[c * Cfg::LD + P] = v;
-  }
+  staged_copy<Cfg::C * G, Cfg::T>(
+      [&](int idx) {
+        const int P = idx / Cfg::C, c = idx % Cfg::C;
+        const int p = pad_to_img(P, N, G);
+        return (p >= 0 && Q0 + c < G) ? inter[int64_t(p) * G + Q0 + c] : make_float2(0.f, 0.f);
+      },
+      [&](int idx, float2 v) { sm[(idx % Cfg::C) * Cfg::LD + idx / Cfg::C] = v; });
   __syncthreads();
   fft_block<LOGN, Cfg::C, Cfg::T, -1>(sm, Cfg::LD, tw);
   for (int idx = threadIdx.x; idx < Cfg::C * G; idx += Cfg::T) {
@@ -138,10 +159,12 @@ __device__ __forceinline__ void phi_adj_cols_body(const float2 *__restrict__ Xt2
   constexpr int G = 1 << LOGN;
   extern __shared__ float2 sm[];
   const int Q0 = blk * Cfg::C;
-  for (int idx = threadIdx.x; idx < Cfg::C * G; idx += Cfg::T) {
-    const int P = idx / Cfg::C, c = idx % Cfg::C;
-    sm[c * Cfg::LD + P] = (Q0 + c < G) ? Xt2[int64_t(P) * G + Q0 + c] : make_float2(0.f, 0.f);
-  }
+  staged_copy<Cfg::C * G, Cfg::T>(
+      [&](int idx) {
+        const int P = idx / Cfg::C, c = idx % Cfg::C;
+        return (Q0 + c < G) ? Xt2[int64_t(P) * G + Q0 + c] : make_float2(0.f, 0.f);
+      },
+      [&](int idx, float2 v) { sm[(idx % Cfg::C) * Cfg::LD + idx / Cfg::C] = v; });
   __syncthreads();
   fft_block<LOGN, Cfg::C, Cfg::T, +1>(sm, Cfg::LD, tw);
   for (int idx = threadIdx.x; idx < Cfg::C * N; idx += Cfg::T) {
@@ -174,11 +197,12 @@ __device__ __forceinline__ void phi_adj_rows_body(const float2 *__restrict__ int
   constexpr int G = 1 << LOGN;
   extern __shared__ float2 sm[];
   const int p0 = blk * Cfg::C;
-  for (int idx = threadIdx.x; idx < Cfg::C * G; idx += Cfg::T) {
-    const int c = idx / G, Q = idx % G;
-    const int p = p0 + c;
-    sm[c * Cfg::LD + Q] = (p < N) ? inter[int64_t(p) * G + Q] : make_float2(0.f, 0.f);
-  }
+  staged_copy<Cfg::C * G, Cfg::T>(
+      [&](int idx) {
+        const int p = p0 + idx / G;
+        return (p < N) ? inter[int64_t(p) * G + idx % G] : make_float2(0.f, 0.f);
+      },
+      [&](int idx, float2 v) { sm[(idx / G) * Cfg::LD + idx % G] = v; });
   __syncthreads();
   fft_block<LOGN, Cfg::C, Cfg::T, +1>(sm, Cfg::LD, tw);
   for (int idx = threadIdx.x; idx < Cfg::C * N; idx += Cfg::T) {
@@ -225,10 +249,12 @@ k_fft_rows(const float2 *__restrict__ in, float2 *__restrict__ out, int64_t n_ro
   constexpr int N = 1 << LOGN;
   extern __shared__ float2 sm[];
   const int64_t r0 = int64_t(blockIdx.x) * Cfg::C;
-  for (int idx = threadIdx.x; idx < Cfg::C * N; idx += Cfg::T) {
-    const int c = idx / N, i = idx % N;
-    sm[c * Cfg::LD + i] = (r0 + c < n_rows) ? in[(r0 + c) * N + i] : make_float2(0.f, 0.f);
-  }
+  staged_copy<Cfg::C * N, Cfg::T>(
+      [&](int idx) {
+        const int64_t r = r0 + idx / N;
+        return (r < n_rows) ? in[r * N + idx % N] : make_float2(0.f, 0.f);
+      },
+      [&](int idx, float2 v) { sm[(idx / N) * Cfg::LD + idx % N] = v; });
   __syncthreads();
   fft_block<LOGN, Cfg::C, Cfg::T, DIR>(sm, Cfg::LD, tw);
   for (int idx = threadIdx.x; idx < Cfg::C * N; idx += Cfg::T) {
@@ -246,16 +272,15 @@ k_fft_cols(const float2 *__restrict__ in, float2 *__restrict__ out, int64_t n_co
   constexpr int N = 1 << LOGN;
   extern __shared__ float2 sm[];
   const int64_t g0 = int64_t(blockIdx.x) * Cfg::C;
-  for (int idx = threadIdx.x; idx < Cfg::C * N; idx += Cfg::T) {
-    const int P = idx / Cfg::C, c = idx % Cfg::C;
-    const int64_t gc = g0 + c;
-    float2 v = make_float2(0.f, 0.f);
-    if (gc < n_cols) {
-      const int64_t b = gc >> LOGN, Q = gc & (N - 1);
-      v = in[(b * N + P) * N + Q];
-    }
-    sm[c * Cfg::LD + P] = v;
-  }
+  staged_copy<Cfg::C * N, Cfg::T>(
+      [&](int idx) {
+        const int P = idx / Cfg::C;
+        const int64_t gc = g0 + idx % Cfg::C;
+        if (gc >= n_cols) return make_float2(0.f, 0.f);
+        const int64_t b = gc >> LOGN, Q = gc & (N - 1);
+        return in[(b * N + P) * N + Q];
+      },
+      [&](int idx, float2 v) { sm[(idx % Cfg::C) * Cfg::LD + idx / Cfg::C] = v; });
   __syncthreads();
   fft_block<LOGN, Cfg::C, Cfg::T, DIR>(sm, Cfg::LD, tw);
   for (int idx = threadIdx.x; idx < Cfg::C * N; idx += Cfg::T) {

@@ -4,8 +4,9 @@
 // stage reads all its butterflies into registers, synchronises, and writes the
 // outputs in Stockham (self-sorting) order, so no bit reversal is needed.
 //
-// Twiddles come from a table tw[k] = exp(-2 pi i k / N), k < N, computed once
-// per plan in double precision and rounded to float.
+// Twiddles come from tables tw_n[k] = exp(-2 pi i k / n), k < n, for every power
+// of two n (stored at offset n), computed once in double precision and rounded
+// to float.
 #pragma once
 
 #include "common.cuh"
@@ -37,15 +38,18 @@ __device__ __forceinline__ void small_dft(float2 (&a)[R]) {
   }
 }
 
+// Stage of span Ns: butterfly k < Ns multiplies input r by exp(-+2 pi i k r /
+// (Ns R)), read from the table of length Ns R (lanes with consecutive k read
+// words r apart, not N / (Ns R) r apart as in the length-N table).
 template <int R, int LOGN, int C, int T, int DIR>
-__device__ __forceinline__ void fft_stage(float2 *s, int ld, int Ns, const float2 *__restrict__ tw) {
+__device__ __forceinline__ void fft_stage(float2 *s, int ld, int Ns, const float2 *__restrict__ twtab) {
   constexpr int N = 1 << LOGN;
   constexpr int NB = N / R;
   constexpr int TOT = NB * C;
   constexpr int PER = (TOT + T - 1) / T;
   float2 v[PER][R];
   const int tid = threadIdx.x;
-  const int step = N / (Ns * R);
+  const float2 *tw = twtab + Ns * R;
 #pragma unroll
   for (int i = 0; i < PER; ++i) {
     const int b = tid + i * T;
@@ -57,7 +61,7 @@ __device__ __forceinline__ void fft_stage(float2 *s, int ld, int Ns, const float
       for (int r = 0; r < R; ++r) {
         float2 x = src[j + r * NB];
         if (r > 0) {
-          float2 w = __ldg(&tw[k * r * step]);
+          float2 w = __ldg(&tw[k * r]);
           if (DIR > 0) w.y = -w.y;
           x = cmul(x, w);
         }
@@ -85,15 +89,14 @@ __device__ __forceinline__ void fft_stage(float2 *s, int ld, int Ns, const float
 // (exp(-2 pi i ...)), +1 inverse (unnormalised).  Caller synchronises before.
 template <int LOGN, int C, int T, int DIR>
 __device__ __forceinline__ void fft_block(float2 *s, int ld, const float2 *__restrict__ twtab) {
-  const float2 *tw = twtab + (1 << LOGN);
   int Ns = 1;
   if constexpr (LOGN & 1) {
-    fft_stage<2, LOGN, C, T, DIR>(s, ld, Ns, tw);
+    fft_stage<2, LOGN, C, T, DIR>(s, ld, Ns, twtab);
     Ns = 2;
   }
 #pragma unroll
   for (int st = 0; st < LOGN / 2; ++st) {
-    fft_stage<4, LOGN, C, T, DIR>(s, ld, Ns, tw);
+    fft_stage<4, LOGN, C, T, DIR>(s, ld, Ns, twtab);
     Ns *= 4;
   }
 }
