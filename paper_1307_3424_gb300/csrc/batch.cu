@@ -489,8 +489,9 @@ wproj_status batch_build_impl(wproj_batch *b, const double *uvw, const int64_t *
   for (auto *pl : plans) b->has_cells = b->has_cells && pl->has_cells;
   if (b->has_cells) {
     WPROJ_TRY(b->tile_ent.alloc(sizeof(int64_t) * (tiles + 1)));
-    WPROJ_TRY(b->cell_ent.alloc(sizeof(uint32_t) * std::max<int64_t>(1, nnz)));
-    WPROJ_TRY(b->cell_val.alloc(sizeof(float2) * std::max<int64_t>(1, nnz)));
+    // 4 entries of padding: the gridding reads whole 16-byte words of 4 entries
+    WPROJ_TRY(b->cell_ent.alloc(sizeof(uint32_t) * (nnz + kCellPad)));
+    WPROJ_TRY(b->cell_val.alloc(sizeof(float2) * (nnz + kCellPad)));
   } else {
     b->tile_ent.release();
     b->cell_ent.release();

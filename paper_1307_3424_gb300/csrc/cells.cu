@@ -5,11 +5,13 @@
 // sorted by cell and, within a cell, by row: one packed word per entry
 // (row << 10 | cell within the tile; rows < 2^22) and its value.  The gridding
 // then needs no accumulators: a block owns a tile, its warps take equal slices
-// of the tile's entries in windows of 32, and within a window the lanes of one
-// cell are summed by a segmented shuffle scan (cells are sorted, so a cell's
-// entries are adjacent).  A run of one cell that crosses a window boundary is
-// carried to the next window; a run that crosses a warp boundary is merged by
-// thread 0 in warp order.  Every cell therefore gets a fixed summation order
+// of the tile's entries in windows of 128, a lane four consecutive entries.
+// Cells are sorted, so a cell's entries are adjacent: a lane sums its entries
+// run by run (a run that begins and ends inside the lane is written at once),
+// and the runs open at the lanes' ends are summed across lanes by a segmented
+// shuffle scan.  A run of one cell that crosses a window boundary is carried
+// to the next window; a run that crosses a warp boundary is merged by thread 0
+// in warp order.  Every cell therefore gets a fixed summation order
 // (bit-reproducible), each cell is written once, and the tile's empty cells are
 // zeroed by the same block.  Grids with few tiles split every tile's entries
 // into `parts` contiguous slices, one block each; a block then writes its
@@ -27,7 +29,7 @@ namespace {
 
 constexpr int kCellWarps = 8;
 constexpr unsigned kCellMask = 1023u;
-constexpr int kAheadE = 2, kAheadY = 1;   // gridding load pipeline depths (windows of 32 entries; deeper measured slower)
+constexpr int kCellJ = 4;   // consecutive entries per lane in the gridding
 
 // exclusive scan of v over a block of 1024 threads; returns the thread's prefix
 __device__ __forceinline__ int block_excl_scan_1024(int v, int *wsum) {
@@ -153,48 +155,132 @@ k_grid_cells(const int64_t *__restrict__ tile_ent, const uint32_t *__restrict__ 
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t n = e1 - e0;
   const int64_t a = e0 + n * w / kCellWarps, b = e0 + n * (w + 1) / kCellWarps;
+  static_assert(kCellJ == 4, "a lane takes one 16-byte word of entries");
+  constexpr int J = kCellJ, WIN = 32 * J;
   int carry_cell = -1;          // run left open by the previous window
   float2 carry = make_float2(0.f, 0.f);
   bool head_done = false;       // the warp's first run has been closed
-  // software pipeline: entries and values kAheadE windows ahead, y kAheadY
-  // windows ahead (a window's y needs its entries, loaded kAheadE - kAheadY
-  // windows earlier), so that several windows' loads are in flight per warp
-  auto load_e = [&](int64_t ws) { return ws + lane < b ? __ldg(cell_ent + ws + lane) : 0u; };
-  auto load_v = [&](int64_t ws) {
-    return ws + lane < b ? cell_value<VDT>(cell_val, ws + lane) : make_float2(0.f, 0.f);
+  auto cell_of = [](uint32_t e) { return int(e & kCellMask); };
+  auto term = [](float2 v, float2 yv) {   // conj(v) y
+    return make_float2(v.x * yv.x + v.y * yv.y, v.x * yv.y - v.y * yv.x);
   };
-  auto load_y = [&](int64_t ws, uint32_t e) { return ws + lane < b ? __ldg(y + (e >> 10)) : make_float2(0.f, 0.f); };
-  uint32_t eq[kAheadE];
-  float2 vq[kAheadE], yq[kAheadY];
+  // Windows start at a multiple of 4 entries at or below a, so that lane l's
+  // entries wb + o + 4 l + j (j < 4) are one aligned 16-byte word of entries
+  // and one (16-bit values) or two (f32) aligned 16-byte words of values; the
+  // arrays carry 4 entries of padding for the last word.  Entries outside
+  // [a, b) are loaded but not used.  Offsets within a warp's slice fit 32 bits
+  // (a tile holds <= 2^32 entries, rows < 2^22 with <= 1024 cells each, and a
+  // warp takes an eighth of a tile at most).
+  const int64_t wb = a & ~int64_t(3);
+  const int span = int(b - wb);
+  const int lo = int(a - wb);
+  const uint32_t *__restrict__ ent_w = cell_ent + wb;
+  // software pipeline: entries two windows ahead, values and y one window ahead
+  auto load_e = [&](int o, uint32_t(&e)[J]) {
+    const int li = o + J * lane;
+    if (li < span) {
+      const uint4 q = __ldg(reinterpret_cast<const uint4 *>(ent_w + li));
+      e[0] = q.x; e[1] = q.y; e[2] = q.z; e[3] = q.w;
+    } else {
+      e[0] = e[1] = e[2] = e[3] = 0u;
+    }
+  };
+  auto load_v = [&](int o, float2(&v)[J]) {
+    const int li = o + J * lane;
+    if (li < span) {
+      if constexpr (VDT == WPROJ_VAL_F32) {
+        const float4 *p4 = reinterpret_cast<const float4 *>(static_cast<const float2 *>(cell_val) + wb + li);
+        const float4 q0 = __ldg(p4), q1 = __ldg(p4 + 1);
+        v[0] = make_float2(q0.x, q0.y); v[1] = make_float2(q0.z, q0.w);
+        v[2] = make_float2(q1.x, q1.y); v[3] = make_float2(q1.z, q1.w);
+      } else {
+        const uint4 q = __ldg(reinterpret_cast<const uint4 *>(static_cast<const unsigned *>(cell_val) + wb + li));
+        const unsigned r[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-  for (int k = 0; k < kAheadE; ++k) {
-    eq[k] = load_e(a + 32 * k);
-    vq[k] = load_v(a + 32 * k);
-  }
+        for (int j = 0; j < J; ++j) {
+          if constexpr (VDT == WPROJ_VAL_BF16) v[j] = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&r[j]));
+          else v[j] = __half22float2(*reinterpret_cast<const __half2 *>(&r[j]));
+        }
+      }
+    } else {
 #pragma unroll
-  for (int k = 0; k < kAheadY; ++k) yq[k] = load_y(a + 32 * k, eq[k]);
-  for (int64_t ws = a; ws < b; ws += 32) {
-    const uint32_t e_cur = eq[0];
-    const float2 v_cur = vq[0], y_cur = yq[0];
+      for (int j = 0; j < J; ++j) v[j] = make_float2(0.f, 0.f);
+    }
+  };
+  auto load_y = [&](int o, const uint32_t(&e)[J], float2(&yv)[J]) {
+    const int li = o + J * lane;
 #pragma unroll
-    for (int k = 0; k + 1 < kAheadE; ++k) {
-      eq[k] = eq[k + 1];
-      vq[k] = vq[k + 1];
+    for (int j = 0; j < J; ++j)
+      yv[j] = (li + j >= lo && li + j < span) ? __ldg(y + (e[j] >> 10)) : make_float2(0.f, 0.f);
+  };
+  uint32_t ec[J], en[J], ef[J];
+  float2 vc[J], vn[J], yc[J], yn[J];
+  load_e(0, ec);
+  load_e(WIN, en);
+  load_v(0, vc);
+  load_y(0, ec, yc);
+  for (int o = 0; o < span; o += WIN) {
+    load_e(o + 2 * WIN, ef);
+    load_v(o + WIN, vn);
+    load_y(o + WIN, en, yn);
+    const int li = o + J * lane;
+    const int last_valid = (span - 1 - o) / J < 31 ? (span - 1 - o) / J : 31;
+    // the lane's runs in entry order: the first (cf), interior runs (complete
+    // within the lane: written here), the last (cl, open at the lane's end)
+    int cf = 4096 + lane, cl = 4096 + lane;   // lanes without entries form runs of their own
+    float2 cs = make_float2(0.f, 0.f), fs = make_float2(0.f, 0.f);
+    bool have = false, multi = false;
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      if (li + j >= lo && li + j < span) {
+        const int c = cell_of(ec[j]);
+        const float2 tj = term(vc[j], yc[j]);
+        if (!have) {
+          cf = cl = c;
+          cs = tj;
+          have = true;
+        } else if (c == cl) {
+          cs = cadd(cs, tj);
+        } else {
+          if (!multi) fs = cs;
+          else out[int64_t(cl >> 5) * G + (cl & 31)] = cs;
+          multi = true;
+          cl = c;
+          cs = tj;
+        }
+      }
     }
 #pragma unroll
-    for (int k = 0; k + 1 < kAheadY; ++k) yq[k] = yq[k + 1];
-    eq[kAheadE - 1] = load_e(ws + 32 * kAheadE);
-    vq[kAheadE - 1] = load_v(ws + 32 * kAheadE);
-    yq[kAheadY - 1] = load_y(ws + 32 * kAheadY, eq[kAheadY - 1]);
-    const int last_valid = int(b - ws < 32 ? b - ws : 32) - 1;
-    const bool valid = lane <= last_valid;
-    int cell = 2048 + lane;     // invalid lanes form runs of their own
-    float2 t = make_float2(0.f, 0.f);
-    if (valid) {
-      cell = int(e_cur & kCellMask);
-      t = make_float2(v_cur.x * y_cur.x + v_cur.y * y_cur.y, v_cur.x * y_cur.y - v_cur.y * y_cur.x);   // conj(v) y
+    for (int j = 0; j < J; ++j) {
+      ec[j] = en[j];
+      en[j] = ef[j];
+      vc[j] = vn[j];
+      yc[j] = yn[j];
     }
-    if (carry_cell >= 0 && __shfl_sync(0xffffffffu, cell, 0) != carry_cell) {
+    // does the run open at the previous lane's end (the carry for lane 0) continue here?
+    int prev_cl = __shfl_up_sync(0xffffffffu, cl, 1);
+    if (lane == 0) prev_cl = carry_cell;
+    const bool chain_in = have && prev_cl == cf;
+    if (lane == 0 && chain_in && !multi) cs = cadd(carry, cs);
+    // segmented inclusive scan of the open runs over the lanes; a segment starts
+    // at lane 0, at a lane with several runs and at a lane that starts a new cell
+    const bool head = lane == 0 || multi || !chain_in;
+    const unsigned hm = __ballot_sync(0xffffffffu, head);
+    const int seg = 31 - __clz(hm & (lane == 31 ? 0xffffffffu : ((2u << lane) - 1u)));
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const float ux = __shfl_up_sync(0xffffffffu, cs.x, o);
+      const float uy = __shfl_up_sync(0xffffffffu, cs.y, o);
+      if (lane - o >= seg) cs = make_float2(ux + cs.x, uy + cs.y);
+    }
+    // a lane with several runs closes its first one, continued from the open run before it
+    float2 pre = make_float2(__shfl_up_sync(0xffffffffu, cs.x, 1), __shfl_up_sync(0xffffffffu, cs.y, 1));
+    if (lane == 0) pre = carry;
+    if (multi && chain_in) fs = cadd(pre, fs);
+    // the open run ends here when the next lane does not continue it
+    const bool next_chain = __shfl_down_sync(0xffffffffu, chain_in, 1);
+    const bool closes_last = have && lane < last_valid && !next_chain;
+    if (carry_cell >= 0 && !__shfl_sync(0xffffffffu, chain_in, 0)) {
       // the carried run ended exactly at the window boundary
       if (!head_done) {
         if (lane == 0) {
@@ -206,34 +292,32 @@ k_grid_cells(const int64_t *__restrict__ tile_ent, const uint32_t *__restrict__ 
       } else if (lane == 0) {
         out[int64_t(carry_cell >> 5) * G + (carry_cell & 31)] = carry;
       }
-      carry_cell = -1;
     }
-    if (lane == 0 && cell == carry_cell) t = cadd(t, carry);
-    // segmented inclusive scan: sum over the preceding lanes of the same cell
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const float ux = __shfl_up_sync(0xffffffffu, t.x, o);
-      const float uy = __shfl_up_sync(0xffffffffu, t.y, o);
-      const int uc = __shfl_up_sync(0xffffffffu, cell, o);
-      if (lane >= o && uc == cell) t = make_float2(t.x + ux, t.y + uy);
-    }
-    const int next = __shfl_down_sync(0xffffffffu, cell, 1);
-    const bool closes = valid && lane < last_valid && next != cell;
-    unsigned cm = __ballot_sync(0xffffffffu, closes);
-    if (!head_done && cm) {     // the warp's first closed run may have begun in the previous warp
-      const int hl = __ffs(cm) - 1;
-      if (lane == hl) {
-        h_cell[w] = cell;
-        h_val[w] = t;
+    unsigned fm = __ballot_sync(0xffffffffu, multi);
+    unsigned lm = __ballot_sync(0xffffffffu, closes_last);
+    if (!head_done && (fm | lm)) {   // the warp's first closed run may have begun in the previous warp
+      const int lf = fm ? __ffs(fm) - 1 : 64, ll = lm ? __ffs(lm) - 1 : 64;
+      if (lf <= ll) {
+        if (lane == lf) {
+          h_cell[w] = cf;
+          h_val[w] = fs;
+        }
+        fm &= fm - 1;
+      } else {
+        if (lane == ll) {
+          h_cell[w] = cl;
+          h_val[w] = cs;
+        }
+        lm &= lm - 1;
       }
-      cm &= cm - 1;
+      if (lane == 0) h_closed[w] = 1;
       head_done = true;
-      if (lane == hl) h_closed[w] = 1;
     }
-    if ((cm >> lane) & 1u) out[int64_t(cell >> 5) * G + (cell & 31)] = t;
-    carry_cell = __shfl_sync(0xffffffffu, cell, last_valid);
-    carry.x = __shfl_sync(0xffffffffu, t.x, last_valid);
-    carry.y = __shfl_sync(0xffffffffu, t.y, last_valid);
+    if ((fm >> lane) & 1u) out[int64_t(cf >> 5) * G + (cf & 31)] = fs;
+    if ((lm >> lane) & 1u) out[int64_t(cl >> 5) * G + (cl & 31)] = cs;
+    carry_cell = __shfl_sync(0xffffffffu, cl, last_valid);
+    carry.x = __shfl_sync(0xffffffffu, cs.x, last_valid);
+    carry.y = __shfl_sync(0xffffffffu, cs.y, last_valid);
   }
   if (lane == 0) {
     if (!head_done) h_closed[w] = 0;
@@ -296,8 +380,9 @@ wproj_status build_cells(wproj_plan *p, const int64_t *tptr, const int64_t *cum,
   const int n_tiles = p->g.nT * p->g.nT;
   const int vb = p->g.value_dtype == WPROJ_VAL_F32 ? 8 : 4;
   WPROJ_TRY(p->tile_ent.alloc(sizeof(int64_t) * (n_tiles + 1)));
-  WPROJ_TRY(p->cell_ent.alloc(sizeof(uint32_t) * std::max<int64_t>(1, p->nnz)));
-  WPROJ_TRY(p->cell_val.alloc(int64_t(vb) * std::max<int64_t>(1, p->nnz)));
+  // 4 entries of padding: the gridding reads whole 16-byte words of 4 entries
+  WPROJ_TRY(p->cell_ent.alloc(sizeof(uint32_t) * (p->nnz + kCellPad)));
+  WPROJ_TRY(p->cell_val.alloc(int64_t(vb) * (p->nnz + kCellPad)));
   k_tile_ent<<<ceil_div(n_tiles + 1, 256), 256, 0, s>>>(n_tiles, tptr, cum, n_seg, p->nnz,
                                                        p->tile_ent.as<int64_t>());
   WPROJ_CHECK_LAUNCH("tile entries");

@@ -242,6 +242,7 @@ wproj_status csr_rows(const wproj_plan *p, int64_t k0, int64_t k1, int32_t *col_
 int64_t degrid_partials(const wproj_plan *p);   // partial sums degridding needs
 
 // cells.cu: cell-major gridding of the column format
+constexpr int64_t kCellPad = 4;   // entries of padding after the cell-major copy
 wproj_status build_cells(wproj_plan *p, const int64_t *tptr, const int64_t *cum, int64_t n_seg, cudaStream_t s);
 wproj_status grid_cells(wproj_plan *p, const float2 *y, float2 *Xt2, cudaStream_t s);
 wproj_status rebuild_cells(wproj_plan *p, cudaStream_t s);
