@@ -123,17 +123,24 @@ __global__ void k_scale_y(int64_t m, const float2 *__restrict__ y, const float *
 // y: visibilities, already multiplied by the row scales for 16-bit values.
 // tile_prob / tab (batches): blockIdx.x is a tile of the whole batch
 template <int VDT>
-__global__ void __launch_bounds__(kCellWarps * 32)
+__global__ void __launch_bounds__(kCellWarps * 32, 4)   // four blocks an SM: 64 registers
 k_grid_cells(const int64_t *__restrict__ tile_ent, const uint32_t *__restrict__ cell_ent,
              const void *__restrict__ cell_val, const float2 *__restrict__ y,
              int logG, int nT, const int32_t *__restrict__ tile_prob, const BProb *__restrict__ tab,
              float2 *__restrict__ Xt2, int parts, float2 *__restrict__ partial) {
   __shared__ int h_cell[kCellWarps], t_cell[kCellWarps], h_closed[kCellWarps];
   __shared__ float2 h_val[kCellWarps], t_val[kCellWarps];
-  int tile = blockIdx.x / parts;
-  const int part = blockIdx.x % parts;
+  int tile = blockIdx.x, part = 0;
+  if (parts > 1) {
+    tile = blockIdx.x / parts;
+    part = blockIdx.x - tile * parts;
+  }
   const int64_t te0 = tile_ent[tile], tn = tile_ent[tile + 1] - te0;
-  const int64_t e0 = te0 + tn * part / parts, e1 = te0 + tn * (part + 1) / parts;
+  int64_t e0 = te0, e1 = te0 + tn;
+  if (parts > 1) {
+    e0 = te0 + tn * part / parts;
+    e1 = te0 + tn * (part + 1) / parts;
+  }
   if (tile_prob) {
     const BProb &P = tab[tile_prob[tile]];
     logG = P.logG;
@@ -143,7 +150,7 @@ k_grid_cells(const int64_t *__restrict__ tile_ent, const uint32_t *__restrict__ 
     y += P.vis_off;
   }
   int G = 1 << logG;
-  const int tu = tile / nT, tv = tile % nT;
+  const int tu = tile >> (logG - 5), tv = tile & (nT - 1);   // nT = G / 32
   float2 *out = Xt2 + int64_t(tu * 32) * G + tv * 32;   // cell c at out[(c >> 5) G + (c & 31)]
   if (parts > 1) {                                      // this slice's partial tile (row stride 32)
     out = partial + int64_t(blockIdx.x) * 1024;
@@ -154,8 +161,8 @@ k_grid_cells(const int64_t *__restrict__ tile_ent, const uint32_t *__restrict__ 
 
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t n = e1 - e0;
-  const int64_t a = e0 + n * w / kCellWarps, b = e0 + n * (w + 1) / kCellWarps;
-  static_assert(kCellJ == 4, "a lane takes one 16-byte word of entries");
+  const int64_t a = e0 + (n * w >> 3), b = e0 + (n * (w + 1) >> 3);
+  static_assert(kCellWarps == 8 && kCellJ == 4, "eight warps; a lane takes one 16-byte word of entries");
   constexpr int J = kCellJ, WIN = 32 * J;
   int carry_cell = -1;          // run left open by the previous window
   float2 carry = make_float2(0.f, 0.f);
