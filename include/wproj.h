@@ -116,8 +116,9 @@ typedef struct {
  *                  (CSR order with the pads), zero-padded to 16 B.
  *                (about 4 B per run instead of 4 B per entry).
  * AUTO picks TILE_RUNS when every box is at most 64 x 64 cells (and the grid is
- * at least 32 x 32), else TILE_MASK when segments average >= 256 entries (dense
- * rows), else COLUMNS.  Requesting TILE_RUNS for larger boxes makes
+ * at least 32 x 32) and the values are F32 (or there are more than 2^22 rows),
+ * else TILE_MASK when segments average >= 256 entries (dense rows), else
+ * COLUMNS.  Requesting TILE_RUNS for larger boxes makes
  * wproj_build_kernels return WPROJ_ERR_UNSUPPORTED.  wproj_csr_rows exports any
  * rows in CSR order from every format. */
 typedef enum {

@@ -1005,12 +1005,16 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
       // segment: columns 5x faster)
       // boxes of at most 64 x 64 cells keep one run of cells per grid row: run
       // descriptors (TILE_RUNS) then cost a few per cent of the value bytes
-      // (measured at N=1024/M=2^21: 283 entries in 16.6 runs per row)
+      // (measured at N=1024/M=2^21: 283 entries in 16.6 runs per row).  With
+      // 16-bit values the column form with its cell-major gridding copy is the
+      // faster of the two there (313.9 against 279.9 Phi+Phi^H pairs/s in bf16;
+      // f32: 266.4 against 291.0), when its packed rows fit (m <= 2^22)
       const bool runs_ok = p->box_max <= 64 && g.tile == 32;
+      const bool cols_16 = g.value_dtype != WPROJ_VAL_F32 && m <= (int64_t(1) << 22);
       int fmt = g.index_format;
       if (fmt == WPROJ_INDEX_AUTO)
-        fmt = runs_ok ? WPROJ_INDEX_TILE_RUNS
-                      : ((p->nnz >= 256 * n_seg) ? WPROJ_INDEX_TILE_MASK : WPROJ_INDEX_COLUMNS);
+        fmt = (runs_ok && !cols_16) ? WPROJ_INDEX_TILE_RUNS
+                                    : ((p->nnz >= 256 * n_seg) ? WPROJ_INDEX_TILE_MASK : WPROJ_INDEX_COLUMNS);
       if (fmt == WPROJ_INDEX_TILE_RUNS && !runs_ok)
         return fail(WPROJ_ERR_UNSUPPORTED, "build_kernels: TILE_RUNS needs kernel boxes of at most 64 x 64 cells");
       if (g.tile != 32) fmt = WPROJ_INDEX_COLUMNS;

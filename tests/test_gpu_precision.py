@@ -49,14 +49,18 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
+@pytest.mark.parametrize("fmt", ["auto", "runs", "columns"])
 @pytest.mark.parametrize("vdt", ["f32", "bf16", "f16"])
-def test_precision_form_against_oracle(case, vdt):
+def test_precision_form_against_oracle(case, vdt, fmt):
     wp, wl, prob, geo, dev = case["wproj"], case["wl"], case["prob"], case["geo"], case["dev"]
     tol_val, tol_op = TOL[vdt]
-    plan = wp.Plan(wl.N, prob.L, box="rule", value_dtype=vdt)
+    plan = wp.Plan(wl.N, prob.L, box="rule", value_dtype=vdt, index_format=fmt)
     plan.build_kernels(torch.from_numpy(prob.uvw).to(dev), wl.e)
     c = plan.csr()
-    assert c.index_format == "runs"     # boxes of 32 and 64 cells: run lengths
+    if fmt == "auto":   # boxes of 32 and 64 cells: run lengths for f32, columns for 16-bit values
+        assert c.index_format == ("runs" if vdt == "f32" else "columns")
+    else:
+        assert c.index_format == fmt
     G = geo.G
     num = den = 0.0
     for k in case["rows"]:
@@ -94,7 +98,7 @@ def test_precision_form_against_oracle(case, vdt):
         np.add.at(Gs, cols, np.conj(vals) * yk)
     xa_ref = O.AZ_adj(geo, O.F_adj(geo, Gs.reshape(G, G)))
     err_adj = _rel(xa, xa_ref)
-    print(f"{vdt}: nnz={c.nnz} format={c.index_format} err(G)={err_val:.2e} err(Phi)={err_phi:.2e} "
+    print(f"{vdt}/{fmt}: nnz={c.nnz} format={c.index_format} err(G)={err_val:.2e} err(Phi)={err_phi:.2e} "
           f"err(Phi^H)={err_adj:.2e}")
     assert err_val <= tol_val
     assert err_phi <= tol_op
