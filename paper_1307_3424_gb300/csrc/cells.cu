@@ -232,31 +232,26 @@ k_grid_cells(const int64_t *__restrict__ tile_ent, const uint32_t *__restrict__ 
     load_y(o + WIN, en, yn);
     const int li = o + J * lane;
     const int last_valid = (span - 1 - o) / J < 31 ? (span - 1 - o) / J : 31;
-    // the lane's runs in entry order: the first (cf), interior runs (complete
-    // within the lane: written here), the last (cl, open at the lane's end)
-    int cf = 4096 + lane, cl = 4096 + lane;   // lanes without entries form runs of their own
-    float2 cs = make_float2(0.f, 0.f), fs = make_float2(0.f, 0.f);
-    bool have = false, multi = false;
+    // Branch-free form over the lane's 4 entries: an entry outside [a, b)
+    // takes the cell of its valid neighbour in the lane and the value 0, so it
+    // joins that run without changing its sum; a lane without entries takes a
+    // cell of its own.
+    bool val[J];
+    int c[J];
+    float2 t[J];
 #pragma unroll
     for (int j = 0; j < J; ++j) {
-      if (li + j >= lo && li + j < span) {
-        const int c = cell_of(ec[j]);
-        const float2 tj = term(vc[j], yc[j]);
-        if (!have) {
-          cf = cl = c;
-          cs = tj;
-          have = true;
-        } else if (c == cl) {
-          cs = cadd(cs, tj);
-        } else {
-          if (!multi) fs = cs;
-          else out[int64_t(cl >> 5) * G + (cl & 31)] = cs;
-          multi = true;
-          cl = c;
-          cs = tj;
-        }
-      }
+      val[j] = li + j >= lo && li + j < span;
+      c[j] = val[j] ? cell_of(ec[j]) : -1;
+      t[j] = val[j] ? term(vc[j], yc[j]) : make_float2(0.f, 0.f);
     }
+#pragma unroll
+    for (int j = 1; j < J; ++j) c[j] = val[j] ? c[j] : c[j - 1];       // trailing
+#pragma unroll
+    for (int j = J - 2; j >= 0; --j) c[j] = c[j] >= 0 ? c[j] : c[j + 1];   // leading
+    const bool any = c[0] >= 0;
+#pragma unroll
+    for (int j = 0; j < J; ++j) c[j] = any ? c[j] : 4096 + lane;
 #pragma unroll
     for (int j = 0; j < J; ++j) {
       ec[j] = en[j];
@@ -264,29 +259,53 @@ k_grid_cells(const int64_t *__restrict__ tile_ent, const uint32_t *__restrict__ 
       vc[j] = vn[j];
       yc[j] = yn[j];
     }
+    // in-lane segmented inclusive sums
+    bool bnd[J];
+    float2 sj[J];
+    bnd[0] = false;
+    sj[0] = t[0];
+#pragma unroll
+    for (int j = 1; j < J; ++j) {
+      bnd[j] = c[j] != c[j - 1];
+      sj[j] = bnd[j] ? t[j] : cadd(sj[j - 1], t[j]);
+    }
+    const bool multi = bnd[1] || bnd[2] || bnd[3];
     // does the run open at the previous lane's end (the carry for lane 0) continue here?
-    int prev_cl = __shfl_up_sync(0xffffffffu, cl, 1);
-    if (lane == 0) prev_cl = carry_cell;
-    const bool chain_in = have && prev_cl == cf;
+    int prev_c = __shfl_up_sync(0xffffffffu, c[J - 1], 1);
+    if (lane == 0) prev_c = carry_cell;
+    const bool chain_in = any && prev_c == c[0];
+    // segmented inclusive scan of the runs open at the lanes' ends; a segment
+    // starts at lane 0, at a lane holding a run boundary and at a lane whose
+    // first cell is new
+    float2 cs = sj[J - 1];
     if (lane == 0 && chain_in && !multi) cs = cadd(carry, cs);
-    // segmented inclusive scan of the open runs over the lanes; a segment starts
-    // at lane 0, at a lane with several runs and at a lane that starts a new cell
     const bool head = lane == 0 || multi || !chain_in;
     const unsigned hm = __ballot_sync(0xffffffffu, head);
     const int seg = 31 - __clz(hm & (lane == 31 ? 0xffffffffu : ((2u << lane) - 1u)));
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const float ux = __shfl_up_sync(0xffffffffu, cs.x, o);
-      const float uy = __shfl_up_sync(0xffffffffu, cs.y, o);
-      if (lane - o >= seg) cs = make_float2(ux + cs.x, uy + cs.y);
+    for (int d = 1; d < 32; d <<= 1) {
+      const float ux = __shfl_up_sync(0xffffffffu, cs.x, d);
+      const float uy = __shfl_up_sync(0xffffffffu, cs.y, d);
+      if (lane - d >= seg) cs = make_float2(ux + cs.x, uy + cs.y);
     }
-    // a lane with several runs closes its first one, continued from the open run before it
-    float2 pre = make_float2(__shfl_up_sync(0xffffffffu, cs.x, 1), __shfl_up_sync(0xffffffffu, cs.y, 1));
-    if (lane == 0) pre = carry;
-    if (multi && chain_in) fs = cadd(pre, fs);
-    // the open run ends here when the next lane does not continue it
-    const bool next_chain = __shfl_down_sync(0xffffffffu, chain_in, 1);
-    const bool closes_last = have && lane < last_valid && !next_chain;
+    // the open run before the lane (the carry for lane 0), added to the lane's first run
+    float2 cin = make_float2(__shfl_up_sync(0xffffffffu, cs.x, 1), __shfl_up_sync(0xffffffffu, cs.y, 1));
+    if (lane == 0) cin = carry;
+    if (!chain_in) cin = make_float2(0.f, 0.f);
+    float2 full[J];
+    bool first = true;
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      first = first && !bnd[j];
+      full[j] = first ? cadd(cin, sj[j]) : sj[j];
+    }
+    // entry j closes its run when the next entry is valid and holds another cell
+    const int next_c0 = __shfl_down_sync(0xffffffffu, c[0], 1);
+    const bool next_any = __shfl_down_sync(0xffffffffu, any, 1) && lane < 31;
+    bool cls[J];
+#pragma unroll
+    for (int j = 0; j + 1 < J; ++j) cls[j] = val[j] && val[j + 1] && bnd[j + 1];
+    cls[J - 1] = val[J - 1] && next_any && next_c0 != c[J - 1];
     if (carry_cell >= 0 && !__shfl_sync(0xffffffffu, chain_in, 0)) {
       // the carried run ended exactly at the window boundary
       if (!head_done) {
@@ -300,31 +319,30 @@ k_grid_cells(const int64_t *__restrict__ tile_ent, const uint32_t *__restrict__ 
         out[int64_t(carry_cell >> 5) * G + (carry_cell & 31)] = carry;
       }
     }
-    unsigned fm = __ballot_sync(0xffffffffu, multi);
-    unsigned lm = __ballot_sync(0xffffffffu, closes_last);
-    if (!head_done && (fm | lm)) {   // the warp's first closed run may have begun in the previous warp
-      const int lf = fm ? __ffs(fm) - 1 : 64, ll = lm ? __ffs(lm) - 1 : 64;
-      if (lf <= ll) {
-        if (lane == lf) {
-          h_cell[w] = cf;
-          h_val[w] = fs;
+    // the warp's first closed run may have begun in the previous warp: its
+    // first closing entry is recorded instead of written
+    int hj = -1;
+    const unsigned cm = __ballot_sync(0xffffffffu, cls[0] || cls[1] || cls[2] || cls[3]);
+    if (!head_done && cm) {
+      if (lane == __ffs(cm) - 1) {
+        hj = cls[0] ? 0 : (cls[1] ? 1 : (cls[2] ? 2 : 3));
+#pragma unroll
+        for (int j = 0; j < J; ++j) {   // static indices: the arrays stay in registers
+          if (j == hj) {
+            h_cell[w] = c[j];
+            h_val[w] = full[j];
+          }
         }
-        fm &= fm - 1;
-      } else {
-        if (lane == ll) {
-          h_cell[w] = cl;
-          h_val[w] = cs;
-        }
-        lm &= lm - 1;
+        h_closed[w] = 1;
       }
-      if (lane == 0) h_closed[w] = 1;
       head_done = true;
     }
-    if ((fm >> lane) & 1u) out[int64_t(cf >> 5) * G + (cf & 31)] = fs;
-    if ((lm >> lane) & 1u) out[int64_t(cl >> 5) * G + (cl & 31)] = cs;
-    carry_cell = __shfl_sync(0xffffffffu, cl, last_valid);
-    carry.x = __shfl_sync(0xffffffffu, cs.x, last_valid);
-    carry.y = __shfl_sync(0xffffffffu, cs.y, last_valid);
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+      if (cls[j] && j != hj) out[int64_t(c[j] >> 5) * G + (c[j] & 31)] = full[j];
+    carry_cell = __shfl_sync(0xffffffffu, c[J - 1], last_valid);
+    carry.x = __shfl_sync(0xffffffffu, full[J - 1].x, last_valid);
+    carry.y = __shfl_sync(0xffffffffu, full[J - 1].y, last_valid);
   }
   if (lane == 0) {
     if (!head_done) h_closed[w] = 0;
