@@ -314,17 +314,45 @@ k_sel_hist(const float2 *__restrict__ K, int S, SelState *__restrict__ sel,
   const int64_t hi = min(n, lo + kSelChunk);
   const float2 *Kb = K + int64_t(b) * n;
   unsigned lmax = 0;
-  // (grouping lanes by bin with match / reduce before the atomics measured
-  // slower: 389 against 210 ms of selection per paper-scale build)
-  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-    const float a2 = abs2_rn(Kb[i]);
-    const unsigned key = __float_as_uint(a2);
-    if (LEVEL == 0) lmax = max(lmax, key);
-    if (LEVEL > 0 && (key >> lvl_shift(LEVEL - 1)) != st.prefix) continue;
-    const unsigned bin = (key >> lvl_shift(LEVEL)) & (nb - 1);
-    const unsigned long long q = (unsigned long long)(double(a2) * st.qscale);
-    atomicAdd(&scnt[bin], 1u);
-    atomicAdd(&sq[bin], q);
+  // A thread takes 8 consecutive samples (four 16-byte loads; S^2 and the
+  // chunk bounds are multiples of 8) and adds a run of samples in one bin with
+  // one pair of atomics: neighbouring samples of a kernel have similar
+  // magnitudes, so runs are common and same-bin conflicts between the lanes of
+  // a warp fall.  The sums are integers, so the histogram does not depend on
+  // the grouping.  (Grouping lanes by bin with match / reduce before the
+  // atomics measured slower: 389 against 210 ms of selection per paper-scale
+  // build.)
+  for (int64_t i0 = lo + 8 * int64_t(threadIdx.x); i0 < hi; i0 += 8 * int64_t(blockDim.x)) {
+    float4 pk[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) pk[h] = __ldg(reinterpret_cast<const float4 *>(Kb + i0) + h);
+    unsigned rbin = 0xffffffffu, rcnt = 0;
+    unsigned long long rq = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float4 &v = pk[j >> 1];
+      const float a2 = abs2_rn((j & 1) ? make_float2(v.z, v.w) : make_float2(v.x, v.y));
+      const unsigned key = __float_as_uint(a2);
+      if (LEVEL == 0) lmax = max(lmax, key);
+      if (LEVEL > 0 && (key >> lvl_shift(LEVEL - 1)) != st.prefix) continue;
+      const unsigned bin = (key >> lvl_shift(LEVEL)) & (nb - 1);
+      const unsigned long long q = (unsigned long long)(double(a2) * st.qscale);
+      if (bin != rbin) {
+        if (rcnt) {
+          atomicAdd(&scnt[rbin], rcnt);
+          atomicAdd(&sq[rbin], rq);
+        }
+        rbin = bin;
+        rcnt = 0;
+        rq = 0;
+      }
+      rcnt += 1;
+      rq += q;
+    }
+    if (rcnt) {
+      atomicAdd(&scnt[rbin], rcnt);
+      atomicAdd(&sq[rbin], rq);
+    }
   }
   if (LEVEL == 0) {
     for (int o = 16; o; o >>= 1) lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
@@ -473,17 +501,45 @@ k_tile_count(const float2 *__restrict__ K, int S, const int32_t *__restrict__ id
   const int64_t lo = int64_t(blockIdx.x) * kSelChunk;
   const int64_t hi = min(n, lo + kSelChunk);
   const float2 *Kb = K + int64_t(b) * n;
-  const int logS = 31 - __clz(S);
-  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-    const int iu = int(i >> logS), iv = int(i & (S - 1));
-    const int su = iu < S / 2 ? iu : iu - S, sv = iv < S / 2 ? iv : iv - S;
-    const int cu = ((j0[k].x + su) % g.G + g.G) % g.G;
-    const int cv = ((j0[k].y + sv) % g.G + g.G) % g.G;
-    const int pos = axis_tile_pos(tu, cu / g.tile) * tv.nt + axis_tile_pos(tv, cv / g.tile);
-    if (st.all) { atomicAdd(&gt[pos], 1); continue; }
-    const unsigned key = __float_as_uint(abs2_rn(Kb[i]));
-    if (key > st.thr_key) atomicAdd(&gt[pos], 1);
-    else if (key == st.thr_key) atomicAdd(&eq[pos], 1);
+  const int logS = 31 - __clz(S), logT = 31 - __clz(g.tile);
+  const int Gm = g.G - 1;   // G and the tile side are powers of two
+  const int2 jk = j0[k];
+  // a thread takes 8 consecutive samples of one box row (S^2 and the chunk
+  // bounds are multiples of 8) and adds each run of samples in one tile with
+  // one pair of atomics (integer counts: the grouping does not matter)
+  for (int64_t i0 = lo + 8 * int64_t(threadIdx.x); i0 < hi; i0 += 8 * int64_t(blockDim.x)) {
+    float4 pk[4];
+    if (!st.all) {
+#pragma unroll
+      for (int h = 0; h < 4; ++h) pk[h] = __ldg(reinterpret_cast<const float4 *>(Kb + i0) + h);
+    }
+    const int iu = int(i0 >> logS), iv0 = int(i0 & (S - 1));
+    const int su = iu < S / 2 ? iu : iu - S;
+    const int pu = axis_tile_pos(tu, ((jk.x + su) & Gm) >> logT) * tv.nt;
+    int rpos = -1, rgt = 0, req = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int iv = iv0 + j;
+      const int sv = iv < S / 2 ? iv : iv - S;
+      const int pos = pu + axis_tile_pos(tv, ((jk.y + sv) & Gm) >> logT);
+      int isgt = 1, iseq = 0;
+      if (!st.all) {
+        const float4 &v = pk[j >> 1];
+        const unsigned key = __float_as_uint(abs2_rn((j & 1) ? make_float2(v.z, v.w) : make_float2(v.x, v.y)));
+        isgt = key > st.thr_key;
+        iseq = key == st.thr_key;
+      }
+      if (pos != rpos) {
+        if (rgt) atomicAdd(&gt[rpos], rgt);
+        if (req) atomicAdd(&eq[rpos], req);
+        rpos = pos;
+        rgt = req = 0;
+      }
+      rgt += isgt;
+      req += iseq;
+    }
+    if (rgt) atomicAdd(&gt[rpos], rgt);
+    if (req) atomicAdd(&eq[rpos], req);
   }
   if (use_smem) {
     __syncthreads();
@@ -584,8 +640,8 @@ k_emit(const float2 *__restrict__ K, int S, const int32_t *__restrict__ ids,
       kidx[rr] = 0;
       if (r < TS && lane < TS) {
         const int cu = tile_u * TS + r, cv = tile_v * TS + lane;
-        const int du = ((cu - tu.a) % g.G + g.G) % g.G;
-        const int dv = ((cv - tv.a) % g.G + g.G) % g.G;
+        const int du = (cu - tu.a) & (g.G - 1);   // G is a power of two
+        const int dv = (cv - tv.a) & (g.G - 1);
         if (du < S && dv < S) {
           const int iu = (du + S / 2) & (S - 1), iv = (dv + S / 2) & (S - 1);
           kidx[rr] = iu * S + iv;
