@@ -202,7 +202,7 @@ __global__ void k_coord_tables(int S, double L, int clamp, double *__restrict__ 
 
 struct SelState {
   unsigned long long target, q_above, q_tot;
-  double qscale;        // 2^62 / E_closed
+  int32_t qexp;         // fixed-point scale 2^qexp: the largest power of two <= 2^62 / E_closed
   uint32_t prefix;
   uint32_t maxkey;
   int32_t n_above;
@@ -250,13 +250,17 @@ __global__ void k_box_tables(const int32_t *__restrict__ ids, const double *__re
     wd[b] = w;
     SelState s = {};
     // 2^62 / E: fixed-point energies; with a screen the row energy is at most
-    // E_kb max|A|^2 (Parseval), which keeps the integer sums below 2^62
+    // E_kb max|A|^2 (Parseval), which keeps the integer sums below 2^62.  The
+    // scale is rounded down to a power of two, so that a sample's fixed-point
+    // energy is its FP32 value shifted (exact, no FP64 arithmetic per sample)
     double escale = eu * ev;
     if (sid) {
       escale *= double(scr_max2[sid[k]]);
       bsid[b] = sid[k];
     }
-    s.qscale = 4611686018427387904.0 / escale;
+    int ex = 0;
+    frexp(4611686018427387904.0 / escale, &ex);   // 2^(ex - 1) <= 2^62 / E < 2^ex
+    s.qexp = ex - 1;
     sel[b] = s;
   }
   __syncthreads();
@@ -289,10 +293,24 @@ __global__ void k_box_tables(const int32_t *__restrict__ ids, const double *__re
 
 // ---- energy-weighted radix select ------------------------------------------------
 // Keys are the FP32 bit patterns of |K|^2 (non-negative, so integer order is
-// value order).  Energies are fixed point q = floor(|K|^2 2^62 / E_closed) and
-// summed as integers, so the prefix is exact and independent of order.
+// value order).  Energies are fixed point q = floor(|K|^2 2^qexp), 2^qexp the
+// largest power of two <= 2^62 / E_closed, and summed as integers, so the
+// prefix is exact and independent of order.
 
 __host__ __device__ constexpr int lvl_shift(int L) { return L == 0 ? 20 : (L == 1 ? 9 : 0); }
+
+// floor(a2 2^qexp) for a non-negative finite float a2, by integer shifts of its
+// significand (exact; capped below 2^63)
+__device__ __forceinline__ unsigned long long fixed_energy(float a2, int qexp) {
+  const unsigned bits = __float_as_uint(a2);
+  int e8 = int(bits >> 23);
+  unsigned long long m = bits & 0x7fffffu;
+  if (e8) m |= 0x800000u;
+  else e8 = 1;                      // subnormal: m 2^(1 - 150)
+  const int sh = e8 - 150 + qexp;   // a2 = m 2^(e8 - 150)
+  if (sh >= 0) return m << (sh < 39 ? sh : 39);
+  return sh > -64 ? (m >> -sh) : 0ull;
+}
 __host__ __device__ constexpr int lvl_bits(int L) { return L == 2 ? 9 : 11; }
 
 template <int LEVEL>
@@ -336,7 +354,7 @@ k_sel_hist(const float2 *__restrict__ K, int S, SelState *__restrict__ sel,
       if (LEVEL == 0) lmax = max(lmax, key);
       if (LEVEL > 0 && (key >> lvl_shift(LEVEL - 1)) != st.prefix) continue;
       const unsigned bin = (key >> lvl_shift(LEVEL)) & (nb - 1);
-      const unsigned long long q = (unsigned long long)(double(a2) * st.qscale);
+      const unsigned long long q = fixed_energy(a2, st.qexp);
       if (bin != rbin) {
         if (rcnt) {
           atomicAdd(&scnt[rbin], rcnt);
@@ -464,7 +482,7 @@ k_sel_find(SelState *__restrict__ sel, const unsigned *__restrict__ hcnt,
     if (LEVEL == 2) {
       st.thr_key = st.prefix;
       const unsigned long long qthr =
-          (unsigned long long)(double(__uint_as_float(st.thr_key)) * st.qscale);
+          fixed_energy(__uint_as_float(st.thr_key), st.qexp);
       const unsigned long long rem = st.target - st.q_above;
       long long nt = (qthr > 0) ? (long long)((rem + qthr - 1) / qthr) : (long long)cstar;
       if (nt > (long long)cstar) nt = cstar;
