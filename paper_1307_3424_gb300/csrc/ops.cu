@@ -1,13 +1,15 @@
 // Part II: the measurement operator Phi = G F Z A (Eq. 8) and its adjoint.
 // Kernels for G in the COLUMNS format (TILE_MASK: tiles.cu) and the dispatch:
 //
-//  degridding  y_k = sum_q G[k, q] X[q]          warp per row piece (<= 16384
-//              entries), partial sums reduced per row in a fixed order
-//  gridding    X'[q] = sum_k conj(G[k, q]) y_k    block per chunk of a grid
-//              tile's segment list; every warp accumulates its segments into
-//              a private shared-memory copy of the 32 x 32 tile, the copies are
-//              summed in warp order, chunk partials are summed per tile in chunk
-//              order.  No global atomics; results are bit-reproducible.
+//  degridding  y_k = sum_q G[k, q] X[q]          32, 16, 8 or 4 lanes per row
+//              piece (<= 16384 entries, or a batch's tuned size), partial sums
+//              reduced per row in a fixed order
+//  gridding    X'[q] = sum_k conj(G[k, q]) y_k    from the cell-major copy
+//              (cells.cu) when it exists; otherwise (m > 2^22) block per chunk
+//              of a grid tile's segment list, every warp accumulating its
+//              segments into a private shared-memory copy of the 32 x 32 tile,
+//              the copies summed in warp order, chunk partials summed per tile
+//              in chunk order.  No global atomics; results are bit-reproducible.
 #include "plan.h"
 
 namespace wproj {
