@@ -618,10 +618,12 @@ k_tie_alloc(const int32_t *__restrict__ ids, const int64_t *__restrict__ seg_bas
 
 // ---- emission -------------------------------------------------------------------------
 
-// One block per (box, touched tile) segment.  Warp w handles tile rows 4w..4w+3,
-// lane = tile column, so a ballot is one row of the tile: the selection word of
-// the tile-mask format, and its popcount prefix gives each entry's place in the
-// row-major compacted order.  Ties are taken in the same row-major order.
+// One warp per (box, touched tile) segment, lane = tile column: the warp walks
+// the tile's rows in order, so a ballot is one row of the tile (the selection
+// word of the tile-mask format) and running popcounts give each entry's place
+// in the row-major compacted order and each tie's rank (ties are taken in the
+// same row-major order).  No block barriers: the 8 warps of a block take 8
+// segments.
 __global__ void __launch_bounds__(256)
 k_emit(const float2 *__restrict__ K, int S, const int32_t *__restrict__ ids,
        const int2 *__restrict__ j0, const int64_t *__restrict__ seg_base,
@@ -631,8 +633,6 @@ k_emit(const float2 *__restrict__ K, int S, const int32_t *__restrict__ ids,
        const float *__restrict__ r_max, const int32_t *__restrict__ seg_cnt,
        int32_t *__restrict__ col, int fmt, void *__restrict__ val, int vdt,
        const int64_t *__restrict__ seg_rec, unsigned char *__restrict__ stream, int *__restrict__ err) {
-  __shared__ unsigned tiew[32], selw[32];
-  __shared__ int tiepre[32], selpre[33];
   const int b = blockIdx.y;
   const int k = ids[b];
   const int nt = ntile[k];
@@ -646,94 +646,68 @@ k_emit(const float2 *__restrict__ K, int S, const int32_t *__restrict__ ids,
   const float2 *Kb = K + int64_t(b) * S * S;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
-  for (int seg = blockIdx.x; seg < nt; seg += gridDim.x) {
+  const bool rec = fmt == WPROJ_INDEX_TILE_MASK;
+  const int Gm = g.G - 1;   // G is a power of two
+  for (int seg = blockIdx.x * 8 + w; seg < nt; seg += gridDim.x * 8) {
     const int iu_t = seg / tv.nt, iv_t = seg % tv.nt;
     const int tile_u = axis_tile_at(tu, iu_t, g.nT), tile_v = axis_tile_at(tv, iv_t, g.nT);
     const int64_t sid = seg_base[k] + seg;
-    int kidx[4];
-    bool gt[4], eq[4];
-    for (int rr = 0; rr < 4; ++rr) {
-      const int r = 4 * w + rr;
-      gt[rr] = eq[rr] = false;
-      kidx[rr] = 0;
-      if (r < TS && lane < TS) {
-        const int cu = tile_u * TS + r, cv = tile_v * TS + lane;
-        const int du = (cu - tu.a) & (g.G - 1);   // G is a power of two
-        const int dv = (cv - tv.a) & (g.G - 1);
-        if (du < S && dv < S) {
-          const int iu = (du + S / 2) & (S - 1), iv = (dv + S / 2) & (S - 1);
-          kidx[rr] = iu * S + iv;
-          const unsigned key = __float_as_uint(abs2_rn(Kb[kidx[rr]]));
-          gt[rr] = all || key > thr;
-          eq[rr] = !all && key == thr;
-        }
-      }
-      const unsigned tw = __ballot_sync(0xffffffffu, eq[rr]);
-      if (lane == 0) tiew[r] = tw;
-    }
-    __syncthreads();
-    if (w == 0) {
-      const int c = __popc(tiew[lane]);
-      int inc = c;
-      for (int o = 1; o < 32; o <<= 1) {
-        const int n = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += n;
-      }
-      tiepre[lane] = inc - c;
-    }
-    __syncthreads();
     const int tie0 = seg_tieb[sid];
-    bool sel[4];
-    for (int rr = 0; rr < 4; ++rr) {
-      const int r = 4 * w + rr;
-      const int rank = tie0 + tiepre[r] + __popc(tiew[r] & lt);
-      sel[rr] = gt[rr] || (eq[rr] && rank < ntie);
-      const unsigned sw = __ballot_sync(0xffffffffu, sel[rr]);
-      if (lane == 0) selw[r] = sw;
-    }
-    __syncthreads();
-    if (w == 0) {
-      const int c = __popc(selw[lane]);
-      int inc = c;
-      for (int o = 1; o < 32; o <<= 1) {
-        const int n = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += n;
-      }
-      selpre[lane] = inc - c;
-      if (lane == 31) selpre[32] = inc;
-    }
-    __syncthreads();
     const int cnt = seg_cnt[sid];
-    if (threadIdx.x == 0 && selpre[32] != cnt) atomicOr(err, ERR_EMIT);
     // COLUMNS: entries at seg_off in col / val; TILE_MASK: the segment's record
-    const bool rec = fmt == WPROJ_INDEX_TILE_MASK;
     const int64_t o = rec ? 0 : seg_off[sid];
     unsigned char *rp = rec ? stream + seg_rec[sid] : nullptr;
     void *vdst = rec ? static_cast<void *>(rp + kRecValues) : val;
-    for (int rr = 0; rr < 4; ++rr) {
-      if (!sel[rr]) continue;
-      const int r = 4 * w + rr;
-      const int pos = selpre[r] + __popc(selw[r] & lt);
-      if (pos >= cnt) continue;      // never taken when the two passes agree
-      const int64_t at = o + pos;
-      if (!rec) col[at] = (tile_u * TS + r) * g.G + tile_v * TS + lane;
-      const float2 v = Kb[kidx[rr]];
-      if (vdt == WPROJ_VAL_F32) {
-        reinterpret_cast<float2 *>(vdst)[at] = v;
-      } else if (vdt == WPROJ_VAL_BF16) {
-        reinterpret_cast<__nv_bfloat162 *>(vdst)[at] = __floats2bfloat162_rn(v.x * inv_scale, v.y * inv_scale);
-      } else {
-        reinterpret_cast<__half2 *>(vdst)[at] = __floats2half2_rn(v.x * inv_scale, v.y * inv_scale);
+    const int cv = tile_v * TS + lane;
+    const int dv = (cv - tv.a) & Gm;
+    const bool col_in = lane < TS && dv < S;
+    const int iv = (dv + S / 2) & (S - 1);
+    int tie_run = 0, sel_run = 0;
+    unsigned my_w = 0;    // lane r keeps row r's selection word and prefix
+    int my_pre = 0;
+#pragma unroll 4
+    for (int r = 0; r < 32; ++r) {
+      bool gt = false, eq = false;
+      int kidx = 0;
+      if (r < TS && col_in) {
+        const int du = (tile_u * TS + r - tu.a) & Gm;
+        if (du < S) {
+          kidx = ((du + S / 2) & (S - 1)) * S + iv;
+          const unsigned key = __float_as_uint(abs2_rn(Kb[kidx]));
+          gt = all || key > thr;
+          eq = !all && key == thr;
+        }
       }
+      const unsigned tw = __ballot_sync(0xffffffffu, eq);
+      const int rank = tie0 + tie_run + __popc(tw & lt);
+      const bool sel = gt || (eq && rank < ntie);
+      const unsigned sw = __ballot_sync(0xffffffffu, sel);
+      const int pos = sel_run + __popc(sw & lt);
+      if (sel && pos < cnt) {    // pos < cnt always holds when the two passes agree
+        const int64_t at = o + pos;
+        if (!rec) col[at] = (tile_u * TS + r) * g.G + cv;
+        const float2 v = Kb[kidx];
+        if (vdt == WPROJ_VAL_F32) {
+          reinterpret_cast<float2 *>(vdst)[at] = v;
+        } else if (vdt == WPROJ_VAL_BF16) {
+          reinterpret_cast<__nv_bfloat162 *>(vdst)[at] = __floats2bfloat162_rn(v.x * inv_scale, v.y * inv_scale);
+        } else {
+          reinterpret_cast<__half2 *>(vdst)[at] = __floats2half2_rn(v.x * inv_scale, v.y * inv_scale);
+        }
+      }
+      if (lane == r) {
+        my_w = sw;
+        my_pre = sel_run;
+      }
+      tie_run += __popc(tw);
+      sel_run += __popc(sw);
     }
+    if (lane == 0 && sel_run != cnt) atomicOr(err, ERR_EMIT);
     if (rec) {
-      if (w == 0) {
-        reinterpret_cast<uint32_t *>(rp + kRecHeader)[lane] = selw[lane];
-        reinterpret_cast<uint16_t *>(rp + kRecPrefix)[lane] = uint16_t(selpre[lane]);
-      }
-      if (threadIdx.x == 0) *reinterpret_cast<int4 *>(rp) = make_int4(k, cnt, int(sid), 0);
+      reinterpret_cast<uint32_t *>(rp + kRecHeader)[lane] = my_w;
+      reinterpret_cast<uint16_t *>(rp + kRecPrefix)[lane] = uint16_t(my_pre);
+      if (lane == 0) *reinterpret_cast<int4 *>(rp) = make_int4(k, cnt, int(sid), 0);
     }
-    __syncthreads();
   }
 }
 
@@ -1211,7 +1185,7 @@ wproj_status build_kernels_impl(wproj_plan *p, const double *uvw, int64_t m, dou
           WPROJ_CHECK_LAUNCH("tie alloc");
         } else {
           ScopedTimer t_emit(p, TC_BEMIT, s);
-          const int gx = std::min(box_tiles(S, g), 1024);   // the kernel strides over more
+          const int gx = std::min(ceil_div(box_tiles(S, g), 8), 1024);   // 8 segments a block; strides over more
           k_emit<<<dim3(gx, nb), 256, 0, s>>>(bb.K, S, ids, d_j0.as<int2>(), d_segbase.as<int64_t>(),
                                               d_ntile.as<int32_t>(), g, p->seg_off.as<int64_t>(),
                                               d_tieb.as<int32_t>(), r_thr.as<uint32_t>(), r_ntie.as<int32_t>(),
