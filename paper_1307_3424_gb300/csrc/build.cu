@@ -41,6 +41,7 @@ size_t batch_bytes(int) { return kBuildBatchBytes; }
 constexpr int kMaxBatchBoxes = 16384;     // grid.y limit for per-box launches
 constexpr int kHistBins = 2048;
 constexpr int kSelChunk = 8192;          // entries per histogram block
+constexpr int kRun = 8;   // consecutive samples a thread takes in the histogram and tile counts (16: slower)
 // Work units of the operators, sized from nnz so that small problems still
 // fill the GPU and large ones keep the partial sums small.
 int64_t degrid_piece(int64_t nnz) { return std::min<int64_t>(16384, std::max<int64_t>(512, nnz / (152 * 64))); }
@@ -332,22 +333,22 @@ k_sel_hist(const float2 *__restrict__ K, int S, SelState *__restrict__ sel,
   const int64_t hi = min(n, lo + kSelChunk);
   const float2 *Kb = K + int64_t(b) * n;
   unsigned lmax = 0;
-  // A thread takes 8 consecutive samples (four 16-byte loads; S^2 and the
-  // chunk bounds are multiples of 8) and adds a run of samples in one bin with
+  // A thread takes kRun consecutive samples (16-byte loads; S^2 and the
+  // chunk bounds are multiples of kRun) and adds a run of samples in one bin with
   // one pair of atomics: neighbouring samples of a kernel have similar
   // magnitudes, so runs are common and same-bin conflicts between the lanes of
   // a warp fall.  The sums are integers, so the histogram does not depend on
   // the grouping.  (Grouping lanes by bin with match / reduce before the
   // atomics measured slower: 389 against 210 ms of selection per paper-scale
   // build.)
-  for (int64_t i0 = lo + 8 * int64_t(threadIdx.x); i0 < hi; i0 += 8 * int64_t(blockDim.x)) {
-    float4 pk[4];
+  for (int64_t i0 = lo + kRun * int64_t(threadIdx.x); i0 < hi; i0 += kRun * int64_t(blockDim.x)) {
+    float4 pk[kRun / 2];
 #pragma unroll
-    for (int h = 0; h < 4; ++h) pk[h] = __ldg(reinterpret_cast<const float4 *>(Kb + i0) + h);
+    for (int h = 0; h < kRun / 2; ++h) pk[h] = __ldg(reinterpret_cast<const float4 *>(Kb + i0) + h);
     unsigned rbin = 0xffffffffu, rcnt = 0;
     unsigned long long rq = 0;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
+    for (int j = 0; j < kRun; ++j) {
       const float4 &v = pk[j >> 1];
       const float a2 = abs2_rn((j & 1) ? make_float2(v.z, v.w) : make_float2(v.x, v.y));
       const unsigned key = __float_as_uint(a2);
@@ -522,21 +523,21 @@ k_tile_count(const float2 *__restrict__ K, int S, const int32_t *__restrict__ id
   const int logS = 31 - __clz(S), logT = 31 - __clz(g.tile);
   const int Gm = g.G - 1;   // G and the tile side are powers of two
   const int2 jk = j0[k];
-  // a thread takes 8 consecutive samples of one box row (S^2 and the chunk
-  // bounds are multiples of 8) and adds each run of samples in one tile with
+  // a thread takes kRun consecutive samples of one box row (S >= 16, S^2 and
+  // the chunk bounds are multiples of kRun) and adds each run of samples in one tile with
   // one pair of atomics (integer counts: the grouping does not matter)
-  for (int64_t i0 = lo + 8 * int64_t(threadIdx.x); i0 < hi; i0 += 8 * int64_t(blockDim.x)) {
-    float4 pk[4];
+  for (int64_t i0 = lo + kRun * int64_t(threadIdx.x); i0 < hi; i0 += kRun * int64_t(blockDim.x)) {
+    float4 pk[kRun / 2];
     if (!st.all) {
 #pragma unroll
-      for (int h = 0; h < 4; ++h) pk[h] = __ldg(reinterpret_cast<const float4 *>(Kb + i0) + h);
+      for (int h = 0; h < kRun / 2; ++h) pk[h] = __ldg(reinterpret_cast<const float4 *>(Kb + i0) + h);
     }
     const int iu = int(i0 >> logS), iv0 = int(i0 & (S - 1));
     const int su = iu < S / 2 ? iu : iu - S;
     const int pu = axis_tile_pos(tu, ((jk.x + su) & Gm) >> logT) * tv.nt;
     int rpos = -1, rgt = 0, req = 0;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
+    for (int j = 0; j < kRun; ++j) {
       const int iv = iv0 + j;
       const int sv = iv < S / 2 ? iv : iv - S;
       const int pos = pu + axis_tile_pos(tv, ((jk.y + sv) & Gm) >> logT);
