@@ -447,6 +447,9 @@ def run_ours(args):
     # kernel labels as in profiles/
     deg_name, grid_name = {"mask": ("k_stream_degrid", "k_stream_grid"), "runs": ("k_runs_degrid", "k_runs_grid"),
                            "columns": ("k_degrid", "k_grid_cells")}[fmt]
+    if args.workload == "precision":   # the traffic figures in profiles/ are per workload
+        deg_name += f"_precision_{args.value_dtype}"
+        grid_name += f"_precision_{args.value_dtype}"
     if kst["t_degrid_ms"] >= kst["t_grid_ms"]:
         dom, ms, alg, kname, stored = "degrid", deg_ms, alg_deg, deg_name, stored_deg
     else:
