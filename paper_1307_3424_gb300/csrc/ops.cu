@@ -31,13 +31,37 @@ __device__ __forceinline__ float2 load_val(const void *__restrict__ val, int64_t
   }
 }
 
-constexpr int kDegridBlocksPerSm = 6;   // 40 registers a thread: six resident 256-thread blocks
+// A stored value as loaded (float2, or one 32-bit word of two 16-bit halves)
+// and its conversion, so that prefetched values stay unconverted until used.
+template <int VDT> struct RawVal { using type = unsigned; };
+template <> struct RawVal<WPROJ_VAL_F32> { using type = float2; };
+
+template <int VDT>
+__device__ __forceinline__ typename RawVal<VDT>::type load_raw(const void *__restrict__ val, int64_t i) {
+  if constexpr (VDT == WPROJ_VAL_F32) return __ldg(reinterpret_cast<const float2 *>(val) + i);
+  else return __ldg(reinterpret_cast<const unsigned *>(val) + i);
+}
+
+template <int VDT>
+__device__ __forceinline__ float2 raw_to_float2(typename RawVal<VDT>::type r) {
+  if constexpr (VDT == WPROJ_VAL_F32) {
+    return r;
+  } else if constexpr (VDT == WPROJ_VAL_BF16) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&r));
+  } else {
+    return __half22float2(*reinterpret_cast<const __half2 *>(&r));
+  }
+}
+
+constexpr int kDegridBlocksPerSm = 4;   // 56 registers a thread: four resident 256-thread blocks
 
 // LPP lanes per row piece (32, 16, 8 or 4): 32 / LPP pieces per warp step, so
 // that short pieces still put several independent loads in flight per lane.
 // Each lane takes up to four entries per step (predicated, all issued before
-// the first use), and the next step's piece header is loaded one step ahead,
-// leaving the column -> grid-value chain as the only dependent loads.
+// the first use); the next step's columns and values are loaded while this
+// step's grid values are gathered, and the next piece's header one piece
+// ahead, so the column -> grid-value chain is the only dependent pair of loads
+// and it overlaps the next step's loads.
 template <int VDT, int LPP>
 __global__ void __launch_bounds__(256, kDegridBlocksPerSm)
 k_degrid(int64_t n_pieces, const int64_t *__restrict__ piece_lo, const int32_t *__restrict__ piece_len,
@@ -55,23 +79,41 @@ k_degrid(int64_t n_pieces, const int64_t *__restrict__ piece_lo, const int32_t *
     const int64_t nlo = npc < n_pieces ? piece_lo[npc] : 0;
     const int nlen = npc < n_pieces ? piece_len[npc] : 0;
     float ax = 0.f, ay = 0.f, bx = 0.f, by = 0.f;
-    for (int i = sl; i < len; i += 4 * LPP) {
-      int c[4];
-      float2 v[4], x[4];
+    using Raw = typename RawVal<VDT>::type;
+    int c[4];
+    Raw v[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const bool ok = i + k * LPP < len;
-        c[k] = ok ? __ldg(col + lo + i + k * LPP) : 0;
-        v[k] = ok ? load_val<VDT>(val, lo + i + k * LPP) : make_float2(0.f, 0.f);
-      }
+    for (int k = 0; k < 4; ++k) {
+      const bool ok = sl + k * LPP < len;
+      c[k] = ok ? __ldg(col + lo + sl + k * LPP) : 0;
+      v[k] = ok ? load_raw<VDT>(val, lo + sl + k * LPP) : Raw{};
+    }
+    for (int i = sl; i < len; i += 4 * LPP) {
+      float2 x[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) x[k] = i + k * LPP < len ? __ldg(Xt + c[k]) : make_float2(0.f, 0.f);
+      // the next step's columns and values, in flight with this step's gathers
+      int cn[4];
+      Raw vn[4];
+      const int in = i + 4 * LPP;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const bool ok = in + k * LPP < len;
+        cn[k] = ok ? __ldg(col + lo + in + k * LPP) : 0;
+        vn[k] = ok ? load_raw<VDT>(val, lo + in + k * LPP) : Raw{};
+      }
 #pragma unroll
       for (int k = 0; k < 4; k += 2) {
-        ax = fmaf(v[k].x, x[k].x, ax); ax = fmaf(-v[k].y, x[k].y, ax);
-        ay = fmaf(v[k].x, x[k].y, ay); ay = fmaf(v[k].y, x[k].x, ay);
-        bx = fmaf(v[k + 1].x, x[k + 1].x, bx); bx = fmaf(-v[k + 1].y, x[k + 1].y, bx);
-        by = fmaf(v[k + 1].x, x[k + 1].y, by); by = fmaf(v[k + 1].y, x[k + 1].x, by);
+        const float2 v0 = raw_to_float2<VDT>(v[k]), v1 = raw_to_float2<VDT>(v[k + 1]);
+        ax = fmaf(v0.x, x[k].x, ax); ax = fmaf(-v0.y, x[k].y, ax);
+        ay = fmaf(v0.x, x[k].y, ay); ay = fmaf(v0.y, x[k].x, ay);
+        bx = fmaf(v1.x, x[k + 1].x, bx); bx = fmaf(-v1.y, x[k + 1].y, bx);
+        by = fmaf(v1.x, x[k + 1].y, by); by = fmaf(v1.y, x[k + 1].x, by);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        c[k] = cn[k];
+        v[k] = vn[k];
       }
     }
     ax += bx;
@@ -219,10 +261,11 @@ __global__ void k_grid_reduce(const int32_t *__restrict__ tile_chunk_ptr, const 
 constexpr int kGridWarps = 8;
 
 // Column-format degridding kernels; partial sums per row piece into `partial`.
-// A piece takes the fewest lanes whose four-entry steps cover its average length.
+// A piece takes the fewest lanes whose two four-entry steps cover its average
+// length (the second step's loads overlap the first's gathers).
 wproj_status launch_degrid_cols(wproj_plan *p, const float2 *Xt, float2 *partial, cudaStream_t s) {
   int lpp = 4;
-  while (lpp < 32 && 4 * lpp * p->n_pieces < p->nnz) lpp *= 2;
+  while (lpp < 32 && 8 * lpp * p->n_pieces < p->nnz) lpp *= 2;
   switch (p->g.value_dtype) {
     case WPROJ_VAL_F32:
       return launch_degrid_pieces<WPROJ_VAL_F32>(p->n_pieces, p->piece_lo.as<int64_t>(), p->piece_len.as<int32_t>(),
